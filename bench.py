@@ -1,0 +1,419 @@
+#!/usr/bin/env python3
+"""Benchmark: batched complex-to-complex FFT throughput on one GB300 (or N replicas).
+
+Workload (one step): the plain-method sweep - forward and inverse c2c
+complex64 transforms for N = 2^3 .. 2^12 with batch = 2^26 / N, i.e. 20
+out-of-place calls over the same 512 MiB synthetic input (SplitMix64 uniform
+[-1, 1)), each moving 2^30 algorithmic bytes (16 bytes per complex point: one
+read, one write).  Inputs are larger than L2, so no flush is needed between
+calls.
+
+Printed (rank 0, one JSON line): whole-job GB/s over the timed steps, the
+live roofline of the dominant kernel (CUDA events on its launch stream), the
+end-to-end figure through gbfft_execute_host (host buffers, copies inside the
+timed region), the clocks sampled during the timed region, and the FP64
+oracle timed on the host cores as a CPU baseline.
+
+``--impl reference`` times the FP64 CPU oracle instead (the reference arm):
+same metric and unit, each step a bounded sample of the same workload.
+
+Multi-GPU: ``--gpus N`` under torchrun runs N independent replicas (the
+transform batch shards by rows with no exchange); barrier + max-over-ranks
+timing; value = bytes of all ranks / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Batched C2C FFT GB/s (% HBM peak) vs plain; serving p50/p99 at stated rel. error"
+UNIT = "GB/s"
+SWEEP = [1 << k for k in range(3, 13)]
+TOTAL = 1 << 26            # complex elements per call
+BYTES_PER_CALL = 16 * TOTAL  # algorithmic bytes: 8 read + 8 written per complex
+WORKLOAD = ("plain-method sweep: forward+inverse c2c complex64, N=2^3..2^12, "
+            "batch=2^26/N (512 MiB in + 512 MiB out per call), uniform[-1,1)")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_06803_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = source_digest()
+    with open(path) as f:
+        for line in f:
+            parts = line.split("#")[0].split()
+            if len(parts) == 3 and parts[0] == kernel_key and parts[2] == digest:
+                return float(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling (200 ms) during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.samples = []
+        self.proc = None
+        self.device_index = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        for p in self.samples:
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, p[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# --------------------------------------------------------------------------
+
+def oracle_sweep_once(flat, points_per_call: int, nthreads: int) -> float:
+    """Run the FP64 oracle (recursive radix-2) over `points_per_call` points of
+    every (N, direction) of the sweep; return wall seconds."""
+    import numpy as np
+
+    import oracle
+    t0 = time.perf_counter()
+    for n in SWEEP:
+        rows = max(1, points_per_call // n)
+        x = flat[: rows * n].reshape(rows, n).astype(np.complex128)
+        for sign in (oracle.FORWARD, oracle.INVERSE):
+            oracle.fft_radix2(x, sign, nthreads)
+    return time.perf_counter() - t0
+
+
+def calibrate_oracle(flat, nthreads: int, target_s: float) -> int:
+    probe = 1 << 14
+    dt = max(oracle_sweep_once(flat, probe, nthreads), 1e-4)
+    pts = int(probe * target_s / dt)
+    pts = max(1 << 12, min(TOTAL, 1 << int(math.log2(max(pts, 1)))))
+    return pts
+
+
+def cpu_baseline(flat, target_s: float = 12.0):
+    cores = os.cpu_count() or 1
+    pts = calibrate_oracle(flat, cores, target_s)
+    dt = oracle_sweep_once(flat, pts, cores)
+    nbytes = 16.0 * pts * len(SWEEP) * 2
+    return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 recursive radix-2 oracle, {pts} points per (N, direction) of the sweep "
+                       f"({len(SWEEP)} sizes x 2 directions), {cores} threads over rows, {dt:.1f} s")}
+
+
+def run_reference(args):
+    world, rank = int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_2207_06803_gb300 import synth
+    seed = synth.DEFAULT_SEED if args.seed is None else args.seed
+    cores = os.cpu_count() or 1
+    # One step = the oracle over a bounded sample of the sweep, sized so that
+    # warmup + steps end within a few minutes.
+    budget_s = 150.0 / max(1, args.steps + args.warmup)
+    flat = synth.uniform_flat(seed, 0, 1 << 22)
+    pts = min(calibrate_oracle(flat, cores, budget_s), 1 << 22)
+    for _ in range(args.warmup):
+        oracle_sweep_once(flat, pts, cores)
+    times = [oracle_sweep_once(flat, pts, cores) for _ in range(args.steps)]
+    total = sum(times)
+    nbytes = 16.0 * pts * len(SWEEP) * 2
+    value = nbytes * args.steps / total / 1e9
+    sample = (f"FP64 recursive radix-2 oracle, {pts} points per (N, direction) of the sweep per step, "
+              f"{cores} threads over rows")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_block(seed),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(seed):
+    return {"workload": WORKLOAD, "sizes": SWEEP, "directions": ["forward", "inverse"],
+            "elements_per_call": TOTAL, "algorithmic_bytes_per_call": BYTES_PER_CALL,
+            "calls_per_step": 2 * len(SWEEP), "seed": seed, "layout": "contiguous rows, out of place",
+            "l2": "inputs larger than L2 (512 MiB per call vs 129 MB L2); no flush"}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2207_06803_gb300 import gbfft, synth
+
+    world, rank, local = dist_setup()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for the gbfft arm")
+    torch.cuda.set_device(local)
+    gbfft.lib()
+    seed = synth.DEFAULT_SEED if args.seed is None else args.seed
+    flat = synth.uniform_flat(seed, 0, TOTAL)
+    d_in = torch.from_numpy(flat.view(np.float32)).to("cuda")
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.Stream()
+
+    plans = []
+    for n in SWEEP:
+        for direction in (gbfft.GBFFT_FORWARD, gbfft.GBFFT_INVERSE):
+            plans.append(((n, direction), gbfft.Plan(n, TOTAL // n, direction)))
+    calls = len(plans)
+
+    def step(events=None):
+        for i, (_, p) in enumerate(plans):
+            if events is not None:
+                events[i][0].record(stream)
+            p.execute(d_in, d_out, stream)
+            if events is not None:
+                events[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    dev_index = local
+    clocks = ClockSampler(dev_index)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in range(calls)]
+          for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for s in range(args.steps):
+        step(ev[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    max_ms = max_over_ranks(world, elapsed_ms)
+
+    per_call_ms = [statistics.mean(ev[s][i][0].elapsed_time(ev[s][i][1]) for s in range(args.steps))
+                   for i in range(calls)]
+    per_size = {}
+    for i, ((n, direction), _) in enumerate(plans):
+        d = per_size.setdefault(str(n), {})
+        d["fwd_gbs" if direction < 0 else "inv_gbs"] = BYTES_PER_CALL / (per_call_ms[i] * 1e-3) / 1e9
+    dom = max(range(calls), key=lambda i: per_call_ms[i])
+    (dom_n, dom_dir), dom_plan = plans[dom]
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    achieved = BYTES_PER_CALL / (per_call_ms[dom] * 1e-3) / 1e9
+    info = dom_plan.info()
+    kernel_key = f"stockham_rows_n{dom_n}_{'fwd' if dom_dir < 0 else 'inv'}_v{info['variant']}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(kernel_key), "kernel": kernel_key,
+                "radices": info["radices"], "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_launch": BYTES_PER_CALL}
+
+    # Round-trip accuracy (no oracle on this leg): ||inv(fwd(x)) - N x|| / ||N x|| on 256 rows per size.
+    roundtrip = {}
+    with torch.cuda.stream(stream):
+        for n in SWEEP:
+            rows = 256
+            xs = d_in[: 2 * n * rows]
+            a = torch.empty_like(xs)
+            b = torch.empty_like(xs)
+            with gbfft.Plan(n, rows, gbfft.GBFFT_FORWARD) as pf, gbfft.Plan(n, rows, gbfft.GBFFT_INVERSE) as pi:
+                pf.execute(xs, a, stream)
+                pi.execute(a, b, stream)
+                stream.synchronize()
+            xr = xs.view(rows, n, 2).double()
+            br = b.view(rows, n, 2).double()
+            err = torch.linalg.vector_norm((br - n * xr).reshape(rows, -1), dim=1) / \
+                torch.linalg.vector_norm((n * xr).reshape(rows, -1), dim=1)
+            roundtrip[str(n)] = float(err.max().item())
+
+    # End to end through the public host-buffer entry point: pinned host input
+    # and output; H2D + transform + D2H of every call inside the timed region.
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(2, min(args.steps, 5))
+    h_in = torch.from_numpy(flat.view(np.float32)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    with torch.cuda.stream(stream):
+        for (_, p) in plans[:2]:
+            p.execute_host(h_in, h_out, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for (_, p) in plans:
+            p.execute_host(h_in, h_out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = max_over_ranks(world, e0.elapsed_time(e1))
+    e2e_value = world * e2e_steps * calls * BYTES_PER_CALL / (e2e_ms * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(flat)
+
+    value = world * args.steps * calls * BYTES_PER_CALL / (max_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config_block(seed), parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                    "h2d_bytes_per_step": calls * BYTES_PER_CALL // 2,
+                    "d2h_bytes_per_step": calls * BYTES_PER_CALL // 2,
+                    "path": "gbfft_execute_host (pinned host buffers, 32 MiB chunk ring)"},
+            "gpu_launches": args.steps * calls,
+            "clocks": clk,
+            "per_size_gbs": per_size,
+            "frac_of_hbm_per_size": {k: {kk: vv / peak for kk, vv in v.items()} for k, v in per_size.items()},
+            "roundtrip_rel_l2_max": roundtrip,
+            "gpu": torch.cuda.get_device_name(),
+        }
+        print(json.dumps(line), flush=True)
+    for _, p in plans:
+        p.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * gbfft - batched one-dimensional complex-to-complex FFTs on GB300 (sm_103a).
+ *
+ * The library computes, for every row x of a batch,
+ *
+ *     y = DFT_N x,   DFT_N[m][k] = w_N^(m*k),   w_N = exp(-2*pi*i/N)
+ *
+ * (the DFT matrix of the FFTc paper, Sec. II), by a factorised Stockham
+ * schedule: stages built from the factor types of the general-radix
+ * Cooley-Tukey factorisation (Eq. 2) - a small DFT_r Kronecker-multiplied with
+ * an identity, a diagonal of twiddle factors and a stride permutation - with
+ * the whole schedule of one transform fused into one kernel for N <= 4096 and
+ * Eq. 2's outer split into two passes for larger N.
+ *
+ * Conventions shared by every entry point:
+ *   - Data: interleaved complex64, i.e. (float re, float im) pairs.  Row i of
+ *     a batch starts at complex element i*N.  Pointers passed to execute calls
+ *     are device pointers (unless the name says _host) that the caller owns;
+ *     they must be 16-byte aligned.
+ *   - Direction: GBFFT_FORWARD uses w_N = exp(-2*pi*i/N); GBFFT_INVERSE uses
+ *     exp(+2*pi*i/N) and is unnormalised, so inverse(forward(x)) = N*x.
+ *   - Errors: every call returns a gbfft_status; nothing throws across this
+ *     boundary.  Execute calls are asynchronous on the caller's stream: launch
+ *     errors come back at once, device-side problems are read with
+ *     gbfft_plan_device_status() after the stream has been synchronised.
+ *   - Plans are created on, and must be executed on, the CUDA device that was
+ *     current at creation.  A plan owns its device tables and workspace; one
+ *     plan must not run concurrently on two streams.
+ */
+#ifndef GBFFT_H
+#define GBFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbfft_plan_s *gbfft_plan; /* opaque; owned by the library */
+
+typedef enum {
+    GBFFT_OK = 0,
+    GBFFT_ERR_INVALID_ARG = 1,      /* null pointer, n < 1, batch < 0, bad enum */
+    GBFFT_ERR_UNSUPPORTED_SIZE = 2, /* n has a prime factor the planner does not handle */
+    GBFFT_ERR_ALIGNMENT = 3,        /* a data pointer is not 16-byte aligned */
+    GBFFT_ERR_OVERLAP = 4,          /* in and out overlap without being identical */
+    GBFFT_ERR_OOM = 5,              /* device allocation failed */
+    GBFFT_ERR_BUDGET = 6,           /* request exceeds a memory budget */
+    GBFFT_ERR_CUDA = 7,             /* a CUDA runtime call or launch failed */
+    GBFFT_ERR_TIMEOUT = 8,          /* a bounded wait ran out */
+    GBFFT_ERR_DEVICE_STATUS = 9,    /* a kernel reported an error in its status word */
+    GBFFT_ERR_NOT_FOUND = 10        /* unknown ticket / variant */
+} gbfft_status;
+
+#define GBFFT_FORWARD (-1)
+#define GBFFT_INVERSE (+1)
+
+typedef enum {
+    GBFFT_C2C_F32 = 0 /* complex64 in/out, FP32 arithmetic, FP64-generated twiddles */
+} gbfft_dtype;
+
+/* Human-readable name of a status code (static storage; never NULL). */
+const char *gbfft_status_string(gbfft_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int gbfft_version(void);
+
+/*
+ * Create a plan for `batch` transforms of length `n` (Sec. II DFT_N) in
+ * direction `direction` (GBFFT_FORWARD / GBFFT_INVERSE) and arithmetic `dtype`.
+ * The planner factorises n into a radix schedule (Eq. 2 factor types) and
+ * generates the twiddle table w_N^j, j < n, in FP64 on the device, rounded to
+ * float32.  batch may be 0 (execute is then a no-op).  On success *out holds a
+ * new plan that the caller releases with gbfft_destroy().  Errors:
+ * INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.  *out is set to NULL on error.
+ */
+gbfft_status gbfft_plan_create(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype);
+
+/*
+ * As gbfft_plan_create, but with the single-pass kernel variant forced to
+ * index `variant` of gbfft_variant_info(n, ...) (used by the autotuner and by
+ * tests that cover every variant).  NOT_FOUND if there is no such variant.
+ */
+gbfft_status gbfft_plan_create_variant(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype,
+                                       int variant);
+
+/*
+ * Run the plan: out = DFT_N in (row by row), asynchronously on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  `in` and `out` are
+ * device pointers to batch*n complex64 values, 16-byte aligned; in == out
+ * (in place) is allowed, partial overlap is not.  Errors: INVALID_ARG,
+ * ALIGNMENT, OVERLAP, CUDA.
+ */
+gbfft_status gbfft_execute(gbfft_plan p, const void *in, void *out, void *cuda_stream);
+
+/*
+ * Host-buffer form of gbfft_execute: `in` and `out` are HOST pointers to
+ * batch*n complex64 values (in == out allowed).  The batch is streamed through
+ * a ring of three device staging buffers of about 32 MiB each (allocated by
+ * the plan on the first call and kept until gbfft_destroy): the host-to-device
+ * copy of one chunk, the transform of the previous chunk and the
+ * device-to-host copy of the one before run concurrently on two internal
+ * streams and `cuda_stream`.  The call is asynchronous like gbfft_execute: all
+ * of its work is ordered after earlier work on `cuda_stream`, and later work on
+ * `cuda_stream` (including a synchronise) sees `out` complete.  Page-locked
+ * host memory (cudaHostAlloc / torch pin_memory) is needed for the copies to
+ * overlap; pageable memory works but serialises them.  Errors: INVALID_ARG,
+ * OVERLAP, OOM, CUDA.
+ */
+gbfft_status gbfft_execute_host(gbfft_plan p, const void *in, void *out, void *cuda_stream);
+
+/* Release a plan and its device memory.  NULL is accepted (no-op). */
+gbfft_status gbfft_destroy(gbfft_plan p);
+
+/*
+ * Describe a plan: length, batch, direction, number of stages and their
+ * radices (up to 8 written to `radices`; may be NULL), the single-pass variant
+ * index (-1 if the plan is multi-pass) and the device workspace it holds, in
+ * bytes.  Any output pointer may be NULL.
+ */
+gbfft_status gbfft_plan_info(gbfft_plan p, int64_t *n, int64_t *batch, int *direction, int *nstages,
+                             int *radices, int *variant, size_t *workspace_bytes);
+
+/*
+ * Number of compiled single-pass kernel variants for length n (0 when n is
+ * only reachable through the multi-pass path or not supported).
+ */
+int gbfft_num_variants(int64_t n);
+
+/*
+ * Variant `index` for length n: its radix schedule (stage count + up to 8
+ * radices), transforms per CTA, threads per CTA and dynamic shared memory.
+ * NOT_FOUND for an index out of range.  Output pointers may be NULL.
+ */
+gbfft_status gbfft_variant_info(int64_t n, int index, int *nstages, int *radices, int *rows_per_cta,
+                                int *threads_per_cta, int *smem_bytes);
+
+/*
+ * Read (and clear) the plan's device status word after the stream that ran it
+ * has been synchronised.  GBFFT_OK when no kernel reported a problem, else
+ * DEVICE_STATUS / TIMEOUT.
+ */
+gbfft_status gbfft_plan_device_status(gbfft_plan p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFFT_H */

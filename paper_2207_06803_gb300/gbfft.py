@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the C ABI in ``include/gbfft.h`` (same names).
+
+Argument marshalling only: every step of the transform runs in the CUDA
+kernels of ``libgbfft.so``.  There is no fallback: if the library is missing
+or fails to load, every call raises :class:`GbfftError`.
+
+Functions return plain Python values and raise :class:`GbfftError` carrying
+the ``gbfft_status`` code on failure.  Device pointers may be given as ints
+or as objects with a ``data_ptr()`` method (e.g. ``torch.Tensor``); streams
+as ints (``cudaStream_t`` values), ``None`` (legacy default stream) or
+objects with a ``cuda_stream`` attribute (``torch.cuda.Stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbfft.so")
+
+GBFFT_FORWARD = -1
+GBFFT_INVERSE = +1
+GBFFT_C2C_F32 = 0
+
+STATUS_NAMES = {
+    0: "GBFFT_OK",
+    1: "GBFFT_ERR_INVALID_ARG",
+    2: "GBFFT_ERR_UNSUPPORTED_SIZE",
+    3: "GBFFT_ERR_ALIGNMENT",
+    4: "GBFFT_ERR_OVERLAP",
+    5: "GBFFT_ERR_OOM",
+    6: "GBFFT_ERR_BUDGET",
+    7: "GBFFT_ERR_CUDA",
+    8: "GBFFT_ERR_TIMEOUT",
+    9: "GBFFT_ERR_DEVICE_STATUS",
+    10: "GBFFT_ERR_NOT_FOUND",
+}
+globals().update({v: k for k, v in STATUS_NAMES.items()})
+
+_c_i64 = ctypes.c_int64
+_c_int = ctypes.c_int
+_c_vp = ctypes.c_void_p
+_c_size = ctypes.c_size_t
+_c_i64p = ctypes.POINTER(ctypes.c_int64)
+_c_intp = ctypes.POINTER(ctypes.c_int)
+_c_sizep = ctypes.POINTER(ctypes.c_size_t)
+
+# name -> (restype, argtypes); mirrors include/gbfft.h
+PROTOTYPES = {
+    "gbfft_status_string": (ctypes.c_char_p, [_c_int]),
+    "gbfft_version": (_c_int, []),
+    "gbfft_plan_create": (_c_int, [ctypes.POINTER(_c_vp), _c_i64, _c_i64, _c_int, _c_int]),
+    "gbfft_plan_create_variant": (_c_int, [ctypes.POINTER(_c_vp), _c_i64, _c_i64, _c_int, _c_int, _c_int]),
+    "gbfft_execute": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
+    "gbfft_execute_host": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
+    "gbfft_destroy": (_c_int, [_c_vp]),
+    "gbfft_plan_info": (_c_int, [_c_vp, _c_i64p, _c_i64p, _c_intp, _c_intp, _c_intp, _c_intp, _c_sizep]),
+    "gbfft_num_variants": (_c_int, [_c_i64]),
+    "gbfft_variant_info": (_c_int, [_c_i64, _c_int, _c_intp, _c_intp, _c_intp, _c_intp, _c_intp]),
+    "gbfft_plan_device_status": (_c_int, [_c_vp]),
+}
+
+
+class GbfftError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        super().__init__(f"{where}: {STATUS_NAMES.get(self.status, self.status)}")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load ``libgbfft.so`` (built by ``paper_2207_06803_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise GbfftError(GBFFT_ERR_CUDA, f"{LIB_PATH} is missing; run the build first")
+                handle = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in PROTOTYPES.items():
+                    fn = getattr(handle, name)
+                    fn.restype = res
+                    fn.argtypes = args
+                _lib = handle
+    return _lib
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    return int(x)
+
+
+def _stream(s) -> int:
+    if s is None:
+        return 0
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    return int(s)
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise GbfftError(rc, where)
+
+
+def gbfft_status_string(status: int) -> str:
+    return lib().gbfft_status_string(int(status)).decode()
+
+
+def gbfft_version() -> int:
+    return int(lib().gbfft_version())
+
+
+def gbfft_plan_create(n: int, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32) -> int:
+    h = _c_vp()
+    _check(lib().gbfft_plan_create(ctypes.byref(h), n, batch, direction, dtype), "gbfft_plan_create")
+    return int(h.value)
+
+
+def gbfft_plan_create_variant(n: int, batch: int, direction: int, dtype: int, variant: int) -> int:
+    h = _c_vp()
+    _check(lib().gbfft_plan_create_variant(ctypes.byref(h), n, batch, direction, dtype, variant),
+           "gbfft_plan_create_variant")
+    return int(h.value)
+
+
+def gbfft_execute(plan: int, x_in, x_out, stream=None) -> None:
+    _check(lib().gbfft_execute(plan, _ptr(x_in), _ptr(x_out), _stream(stream)), "gbfft_execute")
+
+
+def gbfft_execute_host(plan: int, host_in, host_out, stream=None) -> None:
+    """Host pointers (ints, or tensors/arrays exposing data_ptr()/ctypes.data)."""
+    def hp(x):
+        if hasattr(x, "ctypes"):
+            return int(x.ctypes.data)
+        return _ptr(x)
+    _check(lib().gbfft_execute_host(plan, hp(host_in), hp(host_out), _stream(stream)), "gbfft_execute_host")
+
+
+def gbfft_destroy(plan: int) -> None:
+    _check(lib().gbfft_destroy(plan), "gbfft_destroy")
+
+
+def gbfft_plan_info(plan: int) -> dict:
+    n, batch = ctypes.c_int64(), ctypes.c_int64()
+    direction, nst, variant = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    radices = (ctypes.c_int * 8)()
+    ws = ctypes.c_size_t()
+    _check(lib().gbfft_plan_info(plan, ctypes.byref(n), ctypes.byref(batch), ctypes.byref(direction),
+                                 ctypes.byref(nst), radices, ctypes.byref(variant), ctypes.byref(ws)),
+           "gbfft_plan_info")
+    return {"n": n.value, "batch": batch.value, "direction": direction.value,
+            "radices": list(radices[: nst.value]), "variant": variant.value, "workspace_bytes": ws.value}
+
+
+def gbfft_num_variants(n: int) -> int:
+    return int(lib().gbfft_num_variants(n))
+
+
+def gbfft_variant_info(n: int, index: int) -> dict:
+    nst, rows, tpb, smem = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    radices = (ctypes.c_int * 8)()
+    _check(lib().gbfft_variant_info(n, index, ctypes.byref(nst), radices, ctypes.byref(rows),
+                                    ctypes.byref(tpb), ctypes.byref(smem)), "gbfft_variant_info")
+    return {"radices": list(radices[: nst.value]), "rows_per_cta": rows.value,
+            "threads_per_cta": tpb.value, "smem_bytes": smem.value}
+
+
+def gbfft_plan_device_status(plan: int) -> int:
+    return int(lib().gbfft_plan_device_status(plan))
+
+
+class Plan:
+    """Owning wrapper: ``with Plan(n, batch) as p: p.execute(x, y, stream)``."""
+
+    def __init__(self, n: int, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32,
+                 variant: int | None = None):
+        if variant is None:
+            self.handle = gbfft_plan_create(n, batch, direction, dtype)
+        else:
+            self.handle = gbfft_plan_create_variant(n, batch, direction, dtype, variant)
+        self.n, self.batch, self.direction = n, batch, direction
+
+    def execute(self, x_in, x_out, stream=None) -> None:
+        gbfft_execute(self.handle, x_in, x_out, stream)
+
+    def execute_host(self, host_in, host_out, stream=None) -> None:
+        gbfft_execute_host(self.handle, host_in, host_out, stream)
+
+    def info(self) -> dict:
+        return gbfft_plan_info(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            gbfft_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
