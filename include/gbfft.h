@@ -86,6 +86,22 @@ gbfft_status gbfft_plan_create_variant(gbfft_plan *out, int64_t n, int64_t batch
                                        int variant);
 
 /*
+ * As gbfft_plan_create, but forcing the two-pass form of Eq. 2,
+ *     DFT_N = (DFT_K (x) I_M) D^N_M (I_K (x) DFT_M) Pi^N_K,   N = K*M,
+ * with outer factor K = k_outer (0 = the planner's choice).  Pass 1 gathers
+ * the K stride-K columns of each row (Pi^N_K), transforms them (I_K (x) DFT_M)
+ * and scales by D^N_M = diag(w_N^(k*j)) at position k*M + j on the way into a
+ * plan-owned workspace of batch*n complex64; pass 2 applies DFT_K across the
+ * workspace columns (DFT_K (x) I_M) and writes `out` in natural order.  This is
+ * the default for lengths with no single-pass kernel (n > 4096).  Both K and M
+ * must be lengths of the column kernels (32, 48, 64, 80, 96, 112, 128, 256,
+ * 512).  Errors as gbfft_plan_create; NOT_FOUND when k_outer does not give a
+ * supported split.
+ */
+gbfft_status gbfft_plan_create_twopass(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype,
+                                       int64_t k_outer);
+
+/*
  * Run the plan: out = DFT_N in (row by row), asynchronously on `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  `in` and `out` are
  * device pointers to batch*n complex64 values, 16-byte aligned; in == out
@@ -121,6 +137,12 @@ gbfft_status gbfft_destroy(gbfft_plan p);
  */
 gbfft_status gbfft_plan_info(gbfft_plan p, int64_t *n, int64_t *batch, int *direction, int *nstages,
                              int *radices, int *variant, size_t *workspace_bytes);
+
+/*
+ * The Eq. 2 split of a plan: *k_outer = K and *m_inner = M for a two-pass
+ * plan, (1, n) for a single-pass plan.  Output pointers may be NULL.
+ */
+gbfft_status gbfft_plan_factors(gbfft_plan p, int64_t *k_outer, int64_t *m_inner);
 
 /*
  * Number of compiled single-pass kernel variants for length n (0 when n is

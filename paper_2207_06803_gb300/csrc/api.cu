@@ -12,7 +12,6 @@ namespace gbfft {
 
 int rows_variants_for(int64_t n, const RowsVariant** out, int max_out) {
     int found = 0;
-    int cnt = 0;
     const RowsVariant* tabs[2];
     int counts[2];
     tabs[0] = rows_variants_pow2(&counts[0]);
@@ -25,14 +24,30 @@ int rows_variants_for(int64_t n, const RowsVariant** out, int max_out) {
             }
         }
     }
-    (void)cnt;
     return found;
 }
 
+int persistent_grid(const RowsVariant& v) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.kfwd, v.tpb, (size_t)v.smem) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
+cudaError_t prepare_rows(const RowsVariant& v) {
+    if (v.smem <= 48 * 1024) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(v.kfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(v.kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
+    return e;
+}
+
 cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, float2* out, const float2* tw,
-                        long long batch, cudaStream_t stream) {
+                        long long batch, int grid_cap, cudaStream_t stream) {
     if (batch <= 0) return cudaSuccess;
-    const long long blocks = (batch + v.rows - 1) / v.rows;
+    long long blocks = (batch + v.rows - 1) / v.rows;
+    if (v.kind == kRowsPersistent && grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
     void* args[] = {(void*)&in, (void*)&out, (void*)&tw, (void*)&batch};
     const void* fn = direction == GBFFT_FORWARD ? v.kfwd : v.kinv;
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.tpb), args, (size_t)v.smem, stream);
@@ -42,15 +57,28 @@ cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, f
 
 using namespace gbfft;
 
+enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1 };
+
 struct gbfft_plan_s {
     int64_t n = 0;
     int64_t batch = 0;
     int direction = GBFFT_FORWARD;
     int dtype = GBFFT_C2C_F32;
     int device = 0;
+    int kind = kPlanSingle;
+    // single pass
     int variant = -1;
     const RowsVariant* rv = nullptr;
+    int grid_cap = 0;  // persistent variants: resident CTAs on the device
     float2* tw = nullptr;
+    // two passes (Eq. 2 with N = K * M)
+    int64_t k_outer = 1, m_inner = 0;
+    const ColsVariant* cv_m = nullptr;  // pass 1: length-M columns
+    const ColsVariant* cv_k = nullptr;  // pass 2: length-K columns
+    float2* tw_m = nullptr;
+    float2* tw_k = nullptr;
+    float2* post = nullptr;  // D^N_M in workspace layout
+    float2* ws = nullptr;    // workspace z, batch * n complex
     int* status = nullptr;
     size_t ws_bytes = 0;
     // host-buffer execution: staging ring and its streams/events (created on first use)
@@ -90,23 +118,64 @@ void free_plan(gbfft_plan p) {
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->s_in) cudaStreamDestroy(p->s_in);
     if (p->s_out) cudaStreamDestroy(p->s_out);
-    if (p->tw) cudaFree(p->tw);
+    float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
+    for (float2* b : bufs)
+        if (b) cudaFree(b);
     if (p->status) cudaFree(p->status);
     delete p;
 }
 
-gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int variant) {
+// Eq. 2 split N = K * M for the two-pass path: M (pass-1 column length) is
+// taken from a preference list; K must also be a registered column length.
+bool choose_split(int64_t n, int64_t k_req, int64_t* k_out, int64_t* m_out) {
+    if (k_req > 0) {
+        if (n % k_req != 0) return false;
+        const int64_t m = n / k_req;
+        if (!cols_variant_for(k_req) || !cols_variant_for(m)) return false;
+        *k_out = k_req;
+        *m_out = m;
+        return true;
+    }
+    static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
+    for (int64_t m : pref) {
+        if (n % m == 0 && cols_variant_for(m) && cols_variant_for(n / m)) {
+            *k_out = n / m;
+            *m_out = m;
+            return true;
+        }
+    }
+    return false;
+}
+
+gbfft_status alloc_stage_tables(float2** dst, int64_t n, const int* radix, int nstages) {
+    const int cnt = stage_twiddle_count(radix, nstages);
+    if (cudaMalloc(dst, sizeof(float2) * (size_t)(cnt > 0 ? cnt : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return GBFFT_ERR_OOM;
+    }
+    return launch_stage_twiddles(*dst, n, radix, nstages, 0) == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
+}
+
+gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int variant,
+                    int64_t k_outer) {
     if (!out) return GBFFT_ERR_INVALID_ARG;
     *out = nullptr;
-    if (n < 1 || batch < 0) return GBFFT_ERR_INVALID_ARG;
+    if (n < 1 || batch < 0 || k_outer < 0) return GBFFT_ERR_INVALID_ARG;
     if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
     if (dtype != GBFFT_C2C_F32) return GBFFT_ERR_INVALID_ARG;
 
     const RowsVariant* cands[kMaxVariantsPerSize];
     const int nc = rows_variants_for(n, cands, kMaxVariantsPerSize);
-    if (nc == 0) return GBFFT_ERR_UNSUPPORTED_SIZE;
-    if (variant < 0) variant = 0;
-    if (variant >= nc) return GBFFT_ERR_NOT_FOUND;
+    int64_t kk = 0, mm = 0;
+    const bool two_pass = k_outer > 0 || (nc == 0 && variant < 0);
+    if (two_pass) {
+        if (!choose_split(n, k_outer, &kk, &mm)) return k_outer > 0 ? GBFFT_ERR_NOT_FOUND : GBFFT_ERR_UNSUPPORTED_SIZE;
+    } else {
+        if (nc == 0) return GBFFT_ERR_UNSUPPORTED_SIZE;
+        if (variant < 0) variant = 0;
+        if (variant >= nc) return GBFFT_ERR_NOT_FOUND;
+    }
 
     gbfft_plan p = new (std::nothrow) gbfft_plan_s();
     if (!p) return GBFFT_ERR_OOM;
@@ -114,35 +183,61 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     p->batch = batch;
     p->direction = direction;
     p->dtype = dtype;
-    p->variant = variant;
-    p->rv = cands[variant];
-    if (cudaGetDevice(&p->device) != cudaSuccess) {
-        delete p;
-        return GBFFT_ERR_CUDA;
-    }
-    if (cudaMalloc(&p->tw, sizeof(float2) * (size_t)n) != cudaSuccess ||
-        cudaMalloc(&p->status, sizeof(int)) != cudaSuccess) {
+    if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
-        return GBFFT_ERR_OOM;
-    }
-    if (p->rv->smem > 48 * 1024) {
-        if (cudaFuncSetAttribute(p->rv->kfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, p->rv->smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(p->rv->kinv, cudaFuncAttributeMaxDynamicSharedMemorySize, p->rv->smem) !=
-                cudaSuccess) {
-            free_plan(p);
-            return GBFFT_ERR_CUDA;
-        }
-    }
-    // Tables are built on the legacy stream and completed before the plan is returned.
-    if (cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess ||
-        launch_twiddle_table(p->tw, n, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
-        free_plan(p);
         return GBFFT_ERR_CUDA;
+    }
+    gbfft_status st = GBFFT_OK;
+    if (two_pass) {
+        p->kind = kPlanTwoPass;
+        p->k_outer = kk;
+        p->m_inner = mm;
+        p->cv_m = cols_variant_for(mm);
+        p->cv_k = cols_variant_for(kk);
+        p->ws_bytes = sizeof(float2) * (size_t)n * (size_t)batch;
+        if (prepare_cols(*p->cv_m) != cudaSuccess || prepare_cols(*p->cv_k) != cudaSuccess) st = GBFFT_ERR_CUDA;
+        if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw_m, mm, p->cv_m->radix, p->cv_m->nstages);
+        if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw_k, kk, p->cv_k->radix, p->cv_k->nstages);
+        if (st == GBFFT_OK) {
+            if (cudaMalloc(&p->post, sizeof(float2) * (size_t)n) != cudaSuccess ||
+                (p->ws_bytes && cudaMalloc(&p->ws, p->ws_bytes) != cudaSuccess)) {
+                cudaGetLastError();
+                st = GBFFT_ERR_OOM;
+            }
+        }
+        if (st == GBFFT_OK && launch_post_twiddles(p->post, n, mm, 0) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    } else {
+        p->kind = kPlanSingle;
+        p->variant = variant;
+        p->rv = cands[variant];
+        if (prepare_rows(*p->rv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+        if (st == GBFFT_OK && p->rv->kind == kRowsPersistent) {
+            p->grid_cap = persistent_grid(*p->rv);
+            if (p->grid_cap <= 0) st = GBFFT_ERR_CUDA;
+        }
+        if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw, n, p->rv->radix, p->rv->nstages);
+    }
+    // Tables are built on the legacy stream and complete before the plan is returned.
+    if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st != GBFFT_OK) {
+        free_plan(p);
+        return st;
     }
     *out = p;
     return GBFFT_OK;
+}
+
+// Enqueue the transform of `rows` rows from `in` to `out` (device pointers).
+cudaError_t run_device(gbfft_plan p, const float2* in, float2* out, int64_t rows, cudaStream_t s) {
+    if (p->kind == kPlanSingle)
+        return launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)rows, p->grid_cap, s);
+    cudaError_t e = launch_cols(*p->cv_m, 1, p->direction, in, p->ws, p->tw_m, p->post, (long long)rows,
+                                (int)p->k_outer, s);
+    if (e != cudaSuccess) return e;
+    return launch_cols(*p->cv_k, 2, p->direction, p->ws, out, p->tw_k, nullptr, (long long)rows,
+                       (int)p->m_inner, s);
 }
 
 }  // namespace
@@ -169,13 +264,26 @@ const char* gbfft_status_string(gbfft_status s) {
 int gbfft_version(void) { return 100; }
 
 gbfft_status gbfft_plan_create(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype) {
-    return create(out, n, batch, direction, dtype, -1);
+    return create(out, n, batch, direction, dtype, -1, 0);
 }
 
 gbfft_status gbfft_plan_create_variant(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype,
                                        int variant) {
     if (variant < 0) return GBFFT_ERR_NOT_FOUND;
-    return create(out, n, batch, direction, dtype, variant);
+    return create(out, n, batch, direction, dtype, variant, 0);
+}
+
+gbfft_status gbfft_plan_create_twopass(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype,
+                                       int64_t k_outer) {
+    if (k_outer < 0) return GBFFT_ERR_INVALID_ARG;
+    if (k_outer == 0) {
+        int64_t kk, mm;
+        if (out) *out = nullptr;
+        if (n < 1) return GBFFT_ERR_INVALID_ARG;
+        if (!choose_split(n, 0, &kk, &mm)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+        k_outer = kk;
+    }
+    return create(out, n, batch, direction, dtype, -1, k_outer);
 }
 
 gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_stream) {
@@ -184,8 +292,7 @@ gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_s
     const size_t bytes = sizeof(float2) * (size_t)p->n * (size_t)p->batch;
     gbfft_status st = check_io(in, out, bytes);
     if (st != GBFFT_OK) return st;
-    cudaError_t e = launch_rows(*p->rv, p->direction, (const float2*)in, (float2*)out, p->tw,
-                                (long long)p->batch, (cudaStream_t)cuda_stream);
+    cudaError_t e = run_device(p, (const float2*)in, (float2*)out, p->batch, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
@@ -230,7 +337,8 @@ gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_ou
     cudaStream_t su = (cudaStream_t)cuda_stream;
     const char* hin = (const char*)host_in;
     char* hout = (char*)host_out;
-    bool ok = cudaEventRecord(p->ev_start, su) == cudaSuccess && cudaStreamWaitEvent(p->s_in, p->ev_start, 0) == cudaSuccess;
+    bool ok = cudaEventRecord(p->ev_start, su) == cudaSuccess &&
+              cudaStreamWaitEvent(p->s_in, p->ev_start, 0) == cudaSuccess;
     int used = 0;
     for (int64_t r0 = 0, c = 0; ok && r0 < p->batch; r0 += p->stage_rows, ++c) {
         const int b = (int)(c % gbfft_plan_s::kRing);
@@ -240,8 +348,7 @@ gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_ou
         ok = ok && cudaMemcpyAsync(p->stage[b], hin + off, nb, cudaMemcpyHostToDevice, p->s_in) == cudaSuccess;
         ok = ok && cudaEventRecord(p->ev_in[b], p->s_in) == cudaSuccess;
         ok = ok && cudaStreamWaitEvent(su, p->ev_in[b], 0) == cudaSuccess;
-        ok = ok && launch_rows(*p->rv, p->direction, p->stage[b], p->stage[b], p->tw, (long long)rows, su) ==
-                       cudaSuccess;
+        ok = ok && run_device(p, p->stage[b], p->stage[b], rows, su) == cudaSuccess;
         ok = ok && cudaEventRecord(p->ev_comp[b], su) == cudaSuccess;
         ok = ok && cudaStreamWaitEvent(p->s_out, p->ev_comp[b], 0) == cudaSuccess;
         ok = ok && cudaMemcpyAsync(hout + off, p->stage[b], nb, cudaMemcpyDeviceToHost, p->s_out) == cudaSuccess;
@@ -263,11 +370,26 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     if (n) *n = p->n;
     if (batch) *batch = p->batch;
     if (direction) *direction = p->direction;
-    if (nstages) *nstages = p->rv->nstages;
+    int ns = 0;
+    int rad[2 * kMaxStages];
+    if (p->kind == kPlanSingle) {
+        for (int i = 0; i < p->rv->nstages; ++i) rad[ns++] = p->rv->radix[i];
+    } else {
+        for (int i = 0; i < p->cv_m->nstages; ++i) rad[ns++] = p->cv_m->radix[i];
+        for (int i = 0; i < p->cv_k->nstages; ++i) rad[ns++] = p->cv_k->radix[i];
+    }
+    if (nstages) *nstages = ns < kMaxStages ? ns : kMaxStages;
     if (radices)
-        for (int i = 0; i < p->rv->nstages; ++i) radices[i] = p->rv->radix[i];
-    if (variant) *variant = p->variant;
+        for (int i = 0; i < ns && i < kMaxStages; ++i) radices[i] = rad[i];
+    if (variant) *variant = p->kind == kPlanSingle ? p->variant : -1;
     if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+    return GBFFT_OK;
+}
+
+gbfft_status gbfft_plan_factors(gbfft_plan p, int64_t* k_outer, int64_t* m_inner) {
+    if (!p) return GBFFT_ERR_INVALID_ARG;
+    if (k_outer) *k_outer = p->kind == kPlanSingle ? 1 : p->k_outer;
+    if (m_inner) *m_inner = p->kind == kPlanSingle ? p->n : p->m_inner;
     return GBFFT_OK;
 }
 

@@ -1,4 +1,4 @@
-// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16}, fully unrolled.
+// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16, 32}, fully unrolled.
 //
 // Each codelet computes A = DFT_r a in place on r complex values held in
 // registers, natural order in and out, with DFT_r[m][k] = w^(m*k) and
@@ -6,7 +6,7 @@
 // are the "DFT(r)" generators of Table I evaluated as straight-line code, the
 // GPU counterpart of the small solved sub-problems a DFT planner bottoms out in
 // (Sec. III).  Composite codelets use the split of Eq. 2 internally
-// (DFT_8 = 2 x 4, DFT_16 = 4 x 4); the odd primes use the symmetric
+// (DFT_8 = 2 x 4, DFT_16 = 4 x 4, DFT_32 = 2 x 16); the odd primes use the symmetric
 // sum/difference form of the direct DFT.
 #pragma once
 #include <cuda_runtime.h>
@@ -114,6 +114,50 @@ struct Dft<S, 16> {
             Dft<S, 4>::run(c);
 #pragma unroll
             for (int j2 = 0; j2 < 4; ++j2) a[j1 + 4 * j2] = c[j2];
+        }
+    }
+};
+
+// cos(pi*j/16), j = 0..8 (sin(pi*j/16) = cos(pi*(8-j)/16)).
+__device__ __forceinline__ constexpr float cos_pi16(int j) {
+    return j == 0 ? 1.0f
+         : j == 1 ? 0.98078528040323044913f
+         : j == 2 ? 0.92387953251128675613f
+         : j == 3 ? 0.83146961230254523708f
+         : j == 4 ? 0.70710678118654752440f
+         : j == 5 ? 0.55557023301960222474f
+         : j == 6 ? 0.38268343236508977173f
+         : j == 7 ? 0.19509032201612826785f
+                  : 0.0f;
+}
+
+// a * w32^j for j in 0..15, w32 = exp(S*2*pi*i/32) = (cos(pi j/16), S sin(pi j/16)).
+template <int S>
+__device__ __forceinline__ float2 mul_w32(float2 a, int j) {
+    if (j == 0) return a;
+    if (j == 8) return mul_si<S>(a);
+    const float c = j < 8 ? cos_pi16(j) : -cos_pi16(16 - j);
+    const float s = j < 8 ? cos_pi16(8 - j) : cos_pi16(j - 8);
+    return mul_const<S>(a, c, s);
+}
+
+// DFT_32: even/odd split (K = 2, M = 16 in Eq. 2).
+template <int S>
+struct Dft<S, 32> {
+    __device__ __forceinline__ static void run(float2* a) {
+        float2 e[16], o[16];
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            e[m] = a[2 * m];
+            o[m] = a[2 * m + 1];
+        }
+        Dft<S, 16>::run(e);
+        Dft<S, 16>::run(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float2 t = mul_w32<S>(o[k], k);
+            a[k] = cadd(e[k], t);
+            a[k + 16] = csub(e[k], t);
         }
     }
 };

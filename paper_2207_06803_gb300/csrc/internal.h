@@ -12,8 +12,15 @@ namespace gbfft {
 
 constexpr int kMaxStages = 8;
 
+enum RowsKind : int {
+    kRowsDirect = 0,      // k_stockham_rows: one tile per CTA
+    kRowsPersistent = 1,  // k_stockham_rows_pf: resident CTAs walk tiles with register prefetch
+    kRowsSmall = 2        // k_stockham_small: one row per thread, tile staged through shared memory
+};
+
 // One compiled single-pass kernel (both directions) for transform length n.
 struct RowsVariant {
+    int kind;               // RowsKind
     int n;                  // transform length
     int e;                  // complex elements each thread holds per stage
     int rows;               // transforms per CTA
@@ -26,6 +33,31 @@ struct RowsVariant {
     const void* kinv;       // __global__ k_stockham_rows<..., S = +1, ...>
 };
 
+// One compiled column-transform length for the two passes of Eq. 2.
+struct ColsVariant {
+    int len;                // column transform length
+    int e;                  // complex elements per thread per stage
+    int c;                  // columns per CTA
+    int tpb;                // threads per CTA
+    int nstages;
+    int radix[kMaxStages];
+    int smem;               // dynamic shared memory, bytes
+    const void* k1f;        // pass 1 (column gather + DFT + D^N_M), forward / inverse
+    const void* k1i;
+    const void* k2f;        // pass 2 (DFT across the columns), forward / inverse
+    const void* k2i;
+};
+
+const ColsVariant* cols_variant_for(int64_t len);
+const ColsVariant* cols_variants(int* count);
+cudaError_t prepare_cols(const ColsVariant& v);
+// pass 1: in = x, out = workspace z, post = D^N_M table; pass 2: in = z, out = y.
+cudaError_t launch_cols(const ColsVariant& v, int pass, int direction, const float2* in, float2* out,
+                        const float2* tw, const float2* post, long long batch, int ncols, cudaStream_t stream);
+
+// D^N_M table in workspace layout: post[k*M + j1] = w_N^(j1*k), k < N/M, j1 < M.
+cudaError_t launch_post_twiddles(float2* post, int64_t n, int64_t m, cudaStream_t stream);
+
 // Per-translation-unit variant tables, gathered by the registry in api.cu.
 const RowsVariant* rows_variants_pow2(int* count);
 const RowsVariant* rows_variants_mixed(int* count);
@@ -33,11 +65,23 @@ const RowsVariant* rows_variants_mixed(int* count);
 // All variants for length n, in preference order (the first is the default).
 int rows_variants_for(int64_t n, const RowsVariant** out, int max_out);
 
-// Launch a rows variant over `batch` contiguous rows.
+// Largest useful grid for a persistent variant on the current device:
+// resident CTAs per SM times the SM count (0 on error).
+int persistent_grid(const RowsVariant& v);
+
+// Make the variant's kernels accept its dynamic shared memory size.
+cudaError_t prepare_rows(const RowsVariant& v);
+
+// Launch a rows variant over `batch` contiguous rows.  `grid_cap` bounds the
+// grid of a persistent variant (see persistent_grid); ignored otherwise.
 cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, float2* out, const float2* tw,
-                        long long batch, cudaStream_t stream);
+                        long long batch, int grid_cap, cudaStream_t stream);
 
 // tw[j] = exp(-2*pi*i*j/n) for j < n, evaluated in FP64 on the device.
 cudaError_t launch_twiddle_table(float2* tw, int64_t n, cudaStream_t stream);
+
+// Stage twiddle blocks of a schedule (see stockham.cuh): entries and launch.
+int stage_twiddle_count(const int* radix, int nstages);
+cudaError_t launch_stage_twiddles(float2* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream);
 
 }  // namespace gbfft

@@ -15,9 +15,22 @@
 // Data movement per CTA: the first stage reads its operands straight from HBM
 // (for each q, consecutive threads read consecutive elements of a row), the
 // stages exchange through shared memory, and the last stage writes straight to
-// HBM (again consecutive threads, consecutive elements).  Twiddles come from a
-// per-plan table tw[e] = exp(-2*pi*i*e/N) (FP64-generated, stored as float2);
-// w_{L'}^(q*k) is tw[q*k*(N/L')], and the inverse uses the conjugate.
+// HBM (again consecutive threads, consecutive elements).  Twiddles come from
+// per-plan stage tables (FP64-generated, stored as float2): for every stage
+// with L > 1, the (R-1) x L block W_s[q-1][k] = w_{L'}^(q*k) = w_N^(q*k*N/L'),
+// stored q-major so that consecutive threads (consecutive k) read consecutive
+// entries; the blocks of successive stages are concatenated.  The inverse
+// uses the conjugate.
+//
+// Three kernel shapes share the stage code:
+//   k_stockham_rows     one tile per CTA, grid = number of tiles;
+//   k_stockham_rows_pf  persistent: grid = resident CTAs, each CTA walks tiles
+//                       and issues the HBM loads of its next tile before it
+//                       computes the current one (register prefetch), so the
+//                       loads overlap the butterflies and exchanges;
+//   k_stockham_small    one whole row per thread for single-codelet lengths,
+//                       with the tile staged through shared memory so that
+//                       both HBM directions use 16-byte coalesced accesses.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -37,9 +50,58 @@ constexpr int smem_elems() {
     return PS ? (T * N - 1) + ((T * N - 1) >> PS) + 1 : T * N;
 }
 
-template <int N, int S, int E, int T, int PS, int L, bool FIRST, int R, int... Rest>
-__device__ __forceinline__ void stages_rows(float2 (&v)[E], const float2* gin, float2* gout, float2* sm,
-                                            const float2* __restrict__ tw, int nvalid) {
+template <int A, int... Rest>
+struct First {
+    static constexpr int value = A;
+};
+
+// Total size of the concatenated stage twiddle blocks of a schedule.
+template <int L, int... Rs>
+struct StageTwiddles;
+template <int L>
+struct StageTwiddles<L> {
+    static constexpr int value = 0;
+};
+template <int L, int R, int... Rest>
+struct StageTwiddles<L, R, Rest...> {
+    static constexpr int value = (L > 1 ? (R - 1) * L : 0) + StageTwiddles<L * R, Rest...>::value;
+};
+
+// Stage-1 operands of this thread's butterflies, straight from HBM.
+template <int N, int E, int T, int R>
+__device__ __forceinline__ void gather_global(float2 (&v)[E], const float2* gin, int nvalid) {
+    constexpr int TPB = T * N / E, NB = E / R, NR = N / R;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int B = tid + u * TPB;
+        const int t = B / NR, j = B % NR;
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            v[u * R + q] = (t < nvalid) ? gin[t * N + j + q * NR] : make_float2(0.f, 0.f);
+    }
+}
+
+// Stage operands from the shared-memory tile.
+template <int N, int E, int T, int PS, int R>
+__device__ __forceinline__ void gather_smem(float2 (&v)[E], const float2* sm) {
+    constexpr int TPB = T * N / E, NB = E / R, NR = N / R;
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int B = tid + u * TPB;
+        const int t = B / NR, j = B % NR;
+#pragma unroll
+        for (int q = 0; q < R; ++q) v[u * R + q] = sm[spad<PS>(t * N + j + q * NR)];
+    }
+}
+
+// Stages from the one whose operands `v` already holds to the end.  SYNC0:
+// synchronise before the first shared-memory write (needed when earlier
+// readers of the tile buffer may still be running).
+template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest>
+__device__ __forceinline__ void run_stages(float2 (&v)[E], float2* gout, float2* sm, const float2* __restrict__ tw,
+                                           int nvalid) {
     constexpr int TPB = T * N / E;
     constexpr int NB = E / R;  // butterflies per thread in this stage
     constexpr int NR = N / R;  // butterflies per row
@@ -49,26 +111,11 @@ __device__ __forceinline__ void stages_rows(float2 (&v)[E], const float2* gin, f
 
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
-        const int B = tid + u * TPB;
-        const int t = B / NR, j = B % NR;
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int n = j + q * NR;
-            if constexpr (FIRST) {
-                v[u * R + q] = (t < nvalid) ? gin[t * N + n] : make_float2(0.f, 0.f);
-            } else {
-                v[u * R + q] = sm[spad<PS>(t * N + n)];
-            }
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < NB; ++u) {
         if constexpr (L > 1) {
             const int B = tid + u * TPB;
             const int k = (B % NR) % L;
 #pragma unroll
-            for (int q = 1; q < R; ++q)
-                v[u * R + q] = twiddle<S>(v[u * R + q], __ldg(&tw[q * k * (N / (L * R))]));
+            for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], __ldg(&tw[TWO + (q - 1) * L + k]));
         }
         Dft<S, R>::run(&v[u * R]);
     }
@@ -84,7 +131,7 @@ __device__ __forceinline__ void stages_rows(float2 (&v)[E], const float2* gin, f
             }
         }
     } else {
-        if constexpr (!FIRST) __syncthreads();  // all reads of the previous exchange are done
+        if constexpr (SYNC0) __syncthreads();
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int B = tid + u * TPB;
@@ -94,8 +141,14 @@ __device__ __forceinline__ void stages_rows(float2 (&v)[E], const float2* gin, f
             for (int q = 0; q < R; ++q) sm[spad<PS>(t * N + b * L * R + q * L + k)] = v[u * R + q];
         }
         __syncthreads();
-        stages_rows<N, S, E, T, PS, L * R, false, Rest...>(v, gin, gout, sm, tw, nvalid);
+        gather_smem<N, E, T, PS, First<Rest...>::value>(v, sm);
+        run_stages<N, S, E, T, PS, true, TWO + (L > 1 ? (R - 1) * L : 0), L * R, Rest...>(v, gout, sm, tw, nvalid);
     }
+}
+
+__device__ __forceinline__ int tile_rows(long long tile, int T, long long batch) {
+    const long long rem = batch - tile * T;
+    return rem < T ? (int)rem : T;
 }
 
 // Batched contiguous rows: row i of `in`/`out` starts at complex element i*N.
@@ -104,11 +157,81 @@ template <int N, int S, int E, int T, int PS, int... Rs>
 __global__ void __launch_bounds__(T * N / E) k_stockham_rows(const float2* in, float2* out,
                                                               const float2* __restrict__ tw, long long batch) {
     extern __shared__ float2 sm[];
-    const long long r0 = (long long)blockIdx.x * T;
-    const long long rem = batch - r0;
-    const int nvalid = rem < T ? (int)rem : T;
+    const long long tile = blockIdx.x;
+    const int nvalid = tile_rows(tile, T, batch);
     float2 v[E];
-    stages_rows<N, S, E, T, PS, 1, true, Rs...>(v, in + r0 * N, out + r0 * N, sm, tw, nvalid);
+    gather_global<N, E, T, First<Rs...>::value>(v, in + tile * T * N, nvalid);
+    run_stages<N, S, E, T, PS, false, 0, 1, Rs...>(v, out + tile * T * N, sm, tw, nvalid);
+}
+
+// Persistent form with register prefetch of the next tile's stage-1 operands.
+// In place is safe: a CTA reads tile i + gridDim.x before it writes tile i,
+// and only this CTA ever writes tile i + gridDim.x.
+template <int N, int S, int E, int T, int PS, int... Rs>
+__global__ void __launch_bounds__(T * N / E) k_stockham_rows_pf(const float2* in, float2* out,
+                                                                 const float2* __restrict__ tw, long long batch) {
+    extern __shared__ float2 sm[];
+    constexpr int R1 = First<Rs...>::value;
+    const long long ntiles = (batch + T - 1) / T;
+    long long tile = blockIdx.x;
+    float2 nxt[E];
+    if (tile < ntiles) gather_global<N, E, T, R1>(nxt, in + tile * T * N, tile_rows(tile, T, batch));
+    for (; tile < ntiles; tile += gridDim.x) {
+        float2 v[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = nxt[e];
+        const long long next = tile + gridDim.x;
+        if (next < ntiles) gather_global<N, E, T, R1>(nxt, in + next * T * N, tile_rows(next, T, batch));
+        run_stages<N, S, E, T, PS, true, 0, 1, Rs...>(v, out + tile * T * N, sm, tw, tile_rows(tile, T, batch));
+    }
+}
+
+// One row per thread (T rows per CTA) for a length with a single codelet.
+// The tile is copied HBM -> shared memory with 16-byte coalesced loads, each
+// thread transforms its row in registers, and the tile goes back with 16-byte
+// coalesced stores.  Row pitch N + 2 complex keeps the per-thread row accesses
+// conflict-free and the 16-byte slots aligned.  Requires even N.
+template <int N, int S, int T>
+__global__ void __launch_bounds__(T) k_stockham_small(const float2* in, float2* out, const float2* __restrict__ tw,
+                                                       long long batch) {
+    static_assert(N % 2 == 0, "staged rows need an even length");
+    constexpr int P = N + 2;
+    extern __shared__ float2 sm[];
+    const long long tile = blockIdx.x;
+    const int nvalid = tile_rows(tile, T, batch);
+    const int tid = threadIdx.x;
+    const float4* g4 = reinterpret_cast<const float4*>(in + tile * T * N);
+    float4* o4 = reinterpret_cast<float4*>(out + tile * T * N);
+    const int nf = nvalid * (N / 2);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const int f = tid + i * T;
+        if (f < nf) {
+            const int row = (2 * f) / N, col = (2 * f) % N;
+            *reinterpret_cast<float4*>(&sm[row * P + col]) = g4[f];
+        }
+    }
+    __syncthreads();
+    float2 v[N];
+#pragma unroll
+    for (int n = 0; n < N; n += 2) {
+        const float4 p = *reinterpret_cast<const float4*>(&sm[tid * P + n]);
+        v[n] = make_float2(p.x, p.y);
+        v[n + 1] = make_float2(p.z, p.w);
+    }
+    Dft<S, N>::run(v);
+#pragma unroll
+    for (int n = 0; n < N; n += 2)
+        *reinterpret_cast<float4*>(&sm[tid * P + n]) = make_float4(v[n].x, v[n].y, v[n + 1].x, v[n + 1].y);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const int f = tid + i * T;
+        if (f < nf) {
+            const int row = (2 * f) / N, col = (2 * f) % N;
+            o4[f] = *reinterpret_cast<const float4*>(&sm[row * P + col]);
+        }
+    }
 }
 
 }  // namespace gbfft

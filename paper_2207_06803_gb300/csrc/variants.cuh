@@ -9,7 +9,8 @@ template <int N, int E, int T, int PS, int... Rs>
 inline RowsVariant make_rows_variant() {
     static_assert(((Rs * ...) == N), "radix schedule must multiply to N");
     static_assert((T * N) % E == 0, "tile must split evenly over threads");
-    return RowsVariant{N,
+    return RowsVariant{kRowsDirect,
+                       N,
                        E,
                        T,
                        T * N / E,
@@ -21,6 +22,40 @@ inline RowsVariant make_rows_variant() {
                        (const void*)&k_stockham_rows<N, +1, E, T, PS, Rs...>};
 }
 
+template <int N, int E, int T, int PS, int... Rs>
+inline RowsVariant make_rows_pf_variant() {
+    static_assert(((Rs * ...) == N), "radix schedule must multiply to N");
+    static_assert((T * N) % E == 0, "tile must split evenly over threads");
+    return RowsVariant{kRowsPersistent,
+                       N,
+                       E,
+                       T,
+                       T * N / E,
+                       PS,
+                       (int)sizeof...(Rs),
+                       {Rs...},
+                       (int)(sizeof...(Rs) > 1 ? smem_elems<T, N, PS>() * sizeof(float2) : 0),
+                       (const void*)&k_stockham_rows_pf<N, -1, E, T, PS, Rs...>,
+                       (const void*)&k_stockham_rows_pf<N, +1, E, T, PS, Rs...>};
+}
+
+template <int N, int T>
+inline RowsVariant make_small_variant() {
+    return RowsVariant{kRowsSmall,
+                       N,
+                       N,
+                       T,
+                       T,
+                       0,
+                       1,
+                       {N},
+                       (int)(T * (N + 2) * sizeof(float2)),
+                       (const void*)&k_stockham_small<N, -1, T>,
+                       (const void*)&k_stockham_small<N, +1, T>};
+}
+
 }  // namespace gbfft
 
 #define GBFFT_ROWS(N, E, T, PS, ...) ::gbfft::make_rows_variant<N, E, T, PS, __VA_ARGS__>()
+#define GBFFT_ROWS_PF(N, E, T, PS, ...) ::gbfft::make_rows_pf_variant<N, E, T, PS, __VA_ARGS__>()
+#define GBFFT_SMALL(N, T) ::gbfft::make_small_variant<N, T>()

@@ -52,6 +52,8 @@ PROTOTYPES = {
     "gbfft_version": (_c_int, []),
     "gbfft_plan_create": (_c_int, [ctypes.POINTER(_c_vp), _c_i64, _c_i64, _c_int, _c_int]),
     "gbfft_plan_create_variant": (_c_int, [ctypes.POINTER(_c_vp), _c_i64, _c_i64, _c_int, _c_int, _c_int]),
+    "gbfft_plan_create_twopass": (_c_int, [ctypes.POINTER(_c_vp), _c_i64, _c_i64, _c_int, _c_int, _c_i64]),
+    "gbfft_plan_factors": (_c_int, [_c_vp, _c_i64p, _c_i64p]),
     "gbfft_execute": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
     "gbfft_execute_host": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
     "gbfft_destroy": (_c_int, [_c_vp]),
@@ -131,6 +133,20 @@ def gbfft_plan_create_variant(n: int, batch: int, direction: int, dtype: int, va
     return int(h.value)
 
 
+def gbfft_plan_create_twopass(n: int, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32,
+                              k_outer: int = 0) -> int:
+    h = _c_vp()
+    _check(lib().gbfft_plan_create_twopass(ctypes.byref(h), n, batch, direction, dtype, k_outer),
+           "gbfft_plan_create_twopass")
+    return int(h.value)
+
+
+def gbfft_plan_factors(plan: int) -> tuple[int, int]:
+    k, m = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().gbfft_plan_factors(plan, ctypes.byref(k), ctypes.byref(m)), "gbfft_plan_factors")
+    return k.value, m.value
+
+
 def gbfft_execute(plan: int, x_in, x_out, stream=None) -> None:
     _check(lib().gbfft_execute(plan, _ptr(x_in), _ptr(x_out), _stream(stream)), "gbfft_execute")
 
@@ -181,8 +197,10 @@ class Plan:
     """Owning wrapper: ``with Plan(n, batch) as p: p.execute(x, y, stream)``."""
 
     def __init__(self, n: int, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32,
-                 variant: int | None = None):
-        if variant is None:
+                 variant: int | None = None, k_outer: int | None = None):
+        if k_outer is not None:
+            self.handle = gbfft_plan_create_twopass(n, batch, direction, dtype, k_outer)
+        elif variant is None:
             self.handle = gbfft_plan_create(n, batch, direction, dtype)
         else:
             self.handle = gbfft_plan_create_variant(n, batch, direction, dtype, variant)
@@ -195,7 +213,9 @@ class Plan:
         gbfft_execute_host(self.handle, host_in, host_out, stream)
 
     def info(self) -> dict:
-        return gbfft_plan_info(self.handle)
+        d = gbfft_plan_info(self.handle)
+        d["k_outer"], d["m_inner"] = gbfft_plan_factors(self.handle)
+        return d
 
     def close(self) -> None:
         if getattr(self, "handle", None):
