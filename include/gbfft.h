@@ -165,6 +165,31 @@ gbfft_status gbfft_variant_info(int64_t n, int index, int *nstages, int *radices
  */
 gbfft_status gbfft_plan_device_status(gbfft_plan p);
 
+/*
+ * Allocation-free two-pass transform (the paper has no counterpart: this is
+ * a deployment convenience of this library).  For callers that cannot
+ * allocate device memory at the time of the call - hosts that own all device
+ * memory through their own fixed arena and forbid further cudaMalloc, or
+ * real-time loops that must not allocate after start-up - this computes
+ * out = DFT_N in for `batch` rows exactly like a two-pass plan from
+ * gbfft_plan_create_twopass(..., 0), without a plan: the workspace and the
+ * twiddle tables live in one static device array of 64 MiB that is part of
+ * the library image, so every GPU that loads the library holds those 64 MiB
+ * until the process exits.  The tables are regenerated on the stream by each
+ * call; `in`/`out` are caller-owned device pointers as for gbfft_execute.
+ * Limits: 8*n*batch bytes of workspace plus the tables (8*n bytes and the
+ * stage blocks, each rounded up to 256 bytes) must fit in the 64 MiB, else
+ * GBFFT_ERR_BUDGET; n must have a two-pass split (UNSUPPORTED_SIZE).  The
+ * first call on a device looks up the array's device address for that device
+ * (a one-time set-up); make that first call before any stream capture.  All
+ * calls share the array and it keeps the last call's contents: calls that
+ * overlap on the GPU race and corrupt each other, so serialise them.  The call
+ * makes no cudaMalloc/cudaFree.  Errors: INVALID_ARG, ALIGNMENT, OVERLAP,
+ * UNSUPPORTED_SIZE, BUDGET, CUDA.
+ */
+gbfft_status gbfft_execute_twopass_noalloc(int64_t n, int64_t batch, int direction, const void *in, void *out,
+                                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

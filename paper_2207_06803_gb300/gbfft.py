@@ -61,6 +61,7 @@ PROTOTYPES = {
     "gbfft_num_variants": (_c_int, [_c_i64]),
     "gbfft_variant_info": (_c_int, [_c_i64, _c_int, _c_intp, _c_intp, _c_intp, _c_intp, _c_intp]),
     "gbfft_plan_device_status": (_c_int, [_c_vp]),
+    "gbfft_execute_twopass_noalloc": (_c_int, [_c_i64, _c_i64, _c_int, _c_vp, _c_vp, _c_vp]),
 }
 
 
@@ -191,6 +192,13 @@ def gbfft_variant_info(n: int, index: int) -> dict:
 
 def gbfft_plan_device_status(plan: int) -> int:
     return int(lib().gbfft_plan_device_status(plan))
+
+
+def gbfft_execute_twopass_noalloc(n: int, batch: int, direction: int, x_in, x_out, stream=None) -> None:
+    """Plan-free two-pass transform whose workspace and tables live in the
+    library's static device array (see include/gbfft.h); allocates nothing."""
+    _check(lib().gbfft_execute_twopass_noalloc(n, batch, direction, _ptr(x_in), _ptr(x_out), _stream(stream)),
+           "gbfft_execute_twopass_noalloc")
 
 
 class Plan:
