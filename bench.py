@@ -50,13 +50,24 @@ FALLBACK_HBM_GBS = 6800.0
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    return ap.parse_args()
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sizes", type=str, default=None,
+                    help="comma-separated subset of the sweep (for small profiling cases)")
+    ap.add_argument("--points-log2", type=int, default=26,
+                    help="complex points per call (default 26: the 512 MiB sweep workload)")
+    args = ap.parse_args()
+    global SWEEP, TOTAL, BYTES_PER_CALL
+    if args.sizes:
+        SWEEP = [int(v) for v in args.sizes.split(",")]
+    TOTAL = 1 << args.points_log2
+    BYTES_PER_CALL = 16 * TOTAL
+    return args
 
 
 # --------------------------------------------------------------------------
@@ -200,11 +211,17 @@ def oracle_sweep_once(flat, points_per_call: int, nthreads: int) -> float:
 
 
 def calibrate_oracle(flat, nthreads: int, target_s: float) -> int:
+    """Points per (N, direction) so that one pass over the sweep takes about
+    target_s seconds (grown until the probe itself is long enough to time)."""
     probe = 1 << 14
-    dt = max(oracle_sweep_once(flat, probe, nthreads), 1e-4)
-    pts = int(probe * target_s / dt)
-    pts = max(1 << 12, min(TOTAL, 1 << int(math.log2(max(pts, 1)))))
-    return pts
+    limit = min(TOTAL, flat.size)
+    while True:
+        dt = oracle_sweep_once(flat, probe, nthreads)
+        if dt >= min(1.0, target_s / 4) or probe >= limit:
+            break
+        probe = min(limit, probe * 4)
+    pts = int(probe * target_s / max(dt, 1e-6))
+    return max(1 << 12, min(limit, 1 << int(math.log2(max(pts, 1)))))
 
 
 def cpu_baseline(flat, target_s: float = 12.0):
@@ -356,6 +373,43 @@ def run_gpu(args):
     # End to end through the public host-buffer entry point: pinned host input
     # and output; H2D + transform + D2H of every call inside the timed region.
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(2, min(args.steps, 5))
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(torch, np, flat, plans, stream, world, e2e_steps, calls)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(flat)
+
+    value = world * args.steps * calls * BYTES_PER_CALL / (max_ms * 1e-3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(config_block(seed), parallelism="replicas" if world > 1 else "single GPU"),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps * calls,
+            "clocks": clk,
+            "per_size_gbs": per_size,
+            "frac_of_hbm_per_size": {k: {kk: vv / peak for kk, vv in v.items()} for k, v in per_size.items()},
+            "roundtrip_rel_l2_max": roundtrip,
+            "gpu": torch.cuda.get_device_name(),
+        }
+        print(json.dumps(line), flush=True)
+    for _, p in plans:
+        p.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_e2e(torch, np, flat, plans, stream, world, e2e_steps, calls):
+    """End to end through gbfft_execute_host: pinned host input and output;
+    H2D + transform + D2H of every call inside the timed region."""
     h_in = torch.from_numpy(flat.view(np.float32)).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
     with torch.cuda.stream(stream):
@@ -374,38 +428,10 @@ def run_gpu(args):
     barrier(world)
     e2e_ms = max_over_ranks(world, e0.elapsed_time(e1))
     e2e_value = world * e2e_steps * calls * BYTES_PER_CALL / (e2e_ms * 1e-3) / 1e9
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(flat)
-
-    value = world * args.steps * calls * BYTES_PER_CALL / (max_ms * 1e-3) / 1e9
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(config_block(seed), parallelism="replicas" if world > 1 else "single GPU"),
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
-                    "h2d_bytes_per_step": calls * BYTES_PER_CALL // 2,
-                    "d2h_bytes_per_step": calls * BYTES_PER_CALL // 2,
-                    "path": "gbfft_execute_host (pinned host buffers, 32 MiB chunk ring)"},
-            "gpu_launches": args.steps * calls,
-            "clocks": clk,
-            "per_size_gbs": per_size,
-            "frac_of_hbm_per_size": {k: {kk: vv / peak for kk, vv in v.items()} for k, v in per_size.items()},
-            "roundtrip_rel_l2_max": roundtrip,
-            "gpu": torch.cuda.get_device_name(),
-        }
-        print(json.dumps(line), flush=True)
-    for _, p in plans:
-        p.close()
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    return {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+            "h2d_bytes_per_step": calls * BYTES_PER_CALL // 2,
+            "d2h_bytes_per_step": calls * BYTES_PER_CALL // 2,
+            "path": "gbfft_execute_host (pinned host buffers, 32 MiB chunk ring)"}
 
 
 def main():
