@@ -166,6 +166,57 @@ gbfft_status gbfft_variant_info(int64_t n, int index, int *nstages, int *radices
 gbfft_status gbfft_plan_device_status(gbfft_plan p);
 
 /*
+ * Ragged batches: `count` independent transforms of uneven lengths n[i]
+ * (each of the form 2^a, 3*2^a, 5*2^a or 7*2^a within [8, 8192]; others give
+ * UNSUPPORTED_SIZE), transform i occupying complex elements
+ * [offsets[i], offsets[i] + n[i]) of both the input and the output buffer
+ * (typically packed back to back).  Transforms must not overlap each other
+ * (OVERLAP).  Each is DFT_{n[i]} of Sec. II in direction `direction`.  The
+ * plan groups the transforms by length, cuts each group into work items of a
+ * tile shape (rows per item) and uploads an item queue ordered longest-first;
+ * gbfft_execute_ragged then runs ONE persistent kernel launch in which every
+ * CTA claims items from the queue until it is empty, replayed from a CUDA
+ * graph (the counter reset and the launch, captured on the first execute and
+ * patched when the buffers change).  The arrays n/offsets are copied; the
+ * caller keeps ownership.  gbfft_plan_info reports n = elements spanned and
+ * batch = count.
+ */
+gbfft_status gbfft_plan_ragged(gbfft_plan *out, const int64_t *n, const int64_t *offsets, int64_t count,
+                               int direction, int dtype);
+
+/* Run a ragged plan on device buffers `in`/`out` (16-byte aligned, in == out
+ * allowed) asynchronously on `cuda_stream` (one graph launch).  INVALID_ARG if
+ * the plan is not a ragged plan. */
+gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void *cuda_stream);
+
+/*
+ * Tile-shape autotuner for a ragged plan: for each length class, heaviest
+ * first, tries 1, 2, 4 and 8 items per full tile (rows per item = T/split),
+ * timing the whole persistent launch on `in`/`out` (median of `reps` after
+ * one warm-up; `out` is overwritten) and keeps the fastest shapes.  *best_ms
+ * (may be NULL) receives the best median time.  Synchronous.
+ */
+gbfft_status gbfft_ragged_autotune(gbfft_plan p, const void *in, void *out, int reps, float *best_ms);
+
+/* Number of work items in the plan's queue (-1 if not a ragged plan). */
+int64_t gbfft_ragged_num_items(gbfft_plan p);
+
+/* The autotuned split of the tile shape for length n (rows per item =
+ * T_n / split), 0 if n has no class in this plan. */
+int gbfft_ragged_tile_split(gbfft_plan p, int64_t n);
+
+/*
+ * Failure injection and its bound (host side; never faults the GPU): mark
+ * queue item `item` ready (nonzero) or not ready (0).  A CTA that claims an
+ * item that is not ready waits for it at most the wait limit
+ * (gbfft_ragged_set_wait_limit, default 200 ms, 1 us .. 10 s), then records
+ * GBFFT_ERR_TIMEOUT in the plan's status word (gbfft_plan_device_status),
+ * leaves that item's output untouched and continues with the queue.
+ */
+gbfft_status gbfft_ragged_set_item_ready(gbfft_plan p, int64_t item, int ready);
+gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
+
+/*
  * Allocation-free two-pass transform (the paper has no counterpart: this is
  * a deployment convenience of this library).  For callers that cannot
  * allocate device memory at the time of the call - hosts that own all device

@@ -57,7 +57,7 @@ cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, f
 
 using namespace gbfft;
 
-enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1 };
+enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1, kPlanRagged = 2 };
 
 struct gbfft_plan_s {
     int64_t n = 0;
@@ -79,6 +79,8 @@ struct gbfft_plan_s {
     float2* tw_k = nullptr;
     float2* post = nullptr;  // D^N_M in workspace layout
     float2* ws = nullptr;    // workspace z, batch * n complex
+    // ragged batch
+    RaggedState* ragged = nullptr;
     int* status = nullptr;
     size_t ws_bytes = 0;
     // host-buffer execution: staging ring and its streams/events (created on first use)
@@ -118,6 +120,7 @@ void free_plan(gbfft_plan p) {
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->s_in) cudaStreamDestroy(p->s_in);
     if (p->s_out) cudaStreamDestroy(p->s_out);
+    if (p->ragged) ragged_destroy(p->ragged);
     float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
     for (float2* b : bufs)
         if (b) cudaFree(b);
@@ -287,7 +290,7 @@ gbfft_status gbfft_plan_create_twopass(gbfft_plan* out, int64_t n, int64_t batch
 }
 
 gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_stream) {
-    if (!p) return GBFFT_ERR_INVALID_ARG;
+    if (!p || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
     if (p->batch == 0) return GBFFT_OK;
     const size_t bytes = sizeof(float2) * (size_t)p->n * (size_t)p->batch;
     gbfft_status st = check_io(in, out, bytes);
@@ -300,7 +303,7 @@ gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_s
 // while chunk c is transformed on the caller's stream, chunk c+1 is being
 // copied in and chunk c-1 copied out on two internal streams.
 gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_out, void* cuda_stream) {
-    if (!p || !host_in || !host_out) return GBFFT_ERR_INVALID_ARG;
+    if (!p || !host_in || !host_out || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
     if (p->batch == 0) return GBFFT_OK;
     const size_t row_bytes = sizeof(float2) * (size_t)p->n;
     const size_t bytes = row_bytes * (size_t)p->batch;
@@ -372,7 +375,9 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     if (direction) *direction = p->direction;
     int ns = 0;
     int rad[2 * kMaxStages];
-    if (p->kind == kPlanSingle) {
+    if (p->kind == kPlanRagged) {
+        // no single schedule: one per length class
+    } else if (p->kind == kPlanSingle) {
         for (int i = 0; i < p->rv->nstages; ++i) rad[ns++] = p->rv->radix[i];
     } else {
         for (int i = 0; i < p->cv_m->nstages; ++i) rad[ns++] = p->cv_m->radix[i];
@@ -387,10 +392,78 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
 }
 
 gbfft_status gbfft_plan_factors(gbfft_plan p, int64_t* k_outer, int64_t* m_inner) {
-    if (!p) return GBFFT_ERR_INVALID_ARG;
+    if (!p || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
     if (k_outer) *k_outer = p->kind == kPlanSingle ? 1 : p->k_outer;
     if (m_inner) *m_inner = p->kind == kPlanSingle ? p->n : p->m_inner;
     return GBFFT_OK;
+}
+
+gbfft_status gbfft_plan_ragged(gbfft_plan* out, const int64_t* n, const int64_t* offsets, int64_t count,
+                               int direction, int dtype) {
+    if (!out) return GBFFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
+    if (dtype != GBFFT_C2C_F32 || !n || !offsets || count < 1) return GBFFT_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < count; ++i) {
+        if (n[i] < 1 || offsets[i] < 0) return GBFFT_ERR_INVALID_ARG;
+        if (!ragged_supported(n[i])) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    }
+    gbfft_plan p = new (std::nothrow) gbfft_plan_s();
+    if (!p) return GBFFT_ERR_OOM;
+    p->kind = kPlanRagged;
+    p->direction = direction;
+    p->dtype = dtype;
+    p->batch = count;
+    if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        free_plan(p);
+        return GBFFT_ERR_CUDA;
+    }
+    gbfft_status st = ragged_create(&p->ragged, n, offsets, count);
+    if (st != GBFFT_OK) {
+        free_plan(p);
+        return st;
+    }
+    p->n = ragged_total(p->ragged);
+    *out = p;
+    return GBFFT_OK;
+}
+
+gbfft_status gbfft_execute_ragged(gbfft_plan p, const void* in, void* out, void* cuda_stream) {
+    if (!p || p->kind != kPlanRagged) return GBFFT_ERR_INVALID_ARG;
+    gbfft_status st = check_io(in, out, sizeof(float2) * (size_t)ragged_total(p->ragged));
+    if (st != GBFFT_OK) return st;
+    return ragged_execute(p->ragged, p->direction, in, out, p->status, (cudaStream_t)cuda_stream);
+}
+
+gbfft_status gbfft_ragged_autotune(gbfft_plan p, const void* in, void* out, int reps, float* best_ms) {
+    if (!p || p->kind != kPlanRagged) return GBFFT_ERR_INVALID_ARG;
+    gbfft_status st = check_io(in, out, sizeof(float2) * (size_t)ragged_total(p->ragged));
+    if (st != GBFFT_OK) return st;
+    return ragged_autotune(p->ragged, p->direction, in, out, p->status, reps, best_ms);
+}
+
+int64_t gbfft_ragged_num_items(gbfft_plan p) {
+    if (!p || p->kind != kPlanRagged) return -1;
+    return ragged_num_items(p->ragged);
+}
+
+gbfft_status gbfft_ragged_set_item_ready(gbfft_plan p, int64_t item, int ready) {
+    if (!p || p->kind != kPlanRagged) return GBFFT_ERR_INVALID_ARG;
+    return ragged_set_item_ready(p->ragged, item, ready);
+}
+
+gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds) {
+    if (!p || p->kind != kPlanRagged || nanoseconds < 1000 || nanoseconds > 10000000000LL)
+        return GBFFT_ERR_INVALID_ARG;
+    ragged_set_wait_ns(p->ragged, (long long)nanoseconds);
+    return GBFFT_OK;
+}
+
+int gbfft_ragged_tile_split(gbfft_plan p, int64_t n) {
+    if (!p || p->kind != kPlanRagged) return 0;
+    return ragged_class_split(p->ragged, n);
 }
 
 int gbfft_num_variants(int64_t n) { return rows_variants_for(n, nullptr, 0); }

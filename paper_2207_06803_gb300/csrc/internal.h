@@ -58,6 +58,23 @@ cudaError_t launch_cols(const ColsVariant& v, int pass, int direction, const flo
 // D^N_M table in workspace layout: post[k*M + j1] = w_N^(j1*k), k < N/M, j1 < M.
 cudaError_t launch_post_twiddles(float2* post, int64_t n, int64_t m, cudaStream_t stream);
 
+// Ragged-batch plans (ragged.cu).
+struct RaggedState;
+gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* offsets, int64_t count);
+void ragged_destroy(RaggedState* r);
+int64_t ragged_total(const RaggedState* r);
+gbfft_status ragged_execute(RaggedState* r, int direction, const void* in, void* out, int* status,
+                            cudaStream_t s);
+gbfft_status ragged_execute_direct(RaggedState* r, int direction, const void* in, void* out, int* status,
+                                   cudaStream_t s);
+int64_t ragged_num_items(const RaggedState* r);
+gbfft_status ragged_set_item_ready(RaggedState* r, int64_t item, int ready);
+void ragged_set_wait_ns(RaggedState* r, long long ns);
+gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void* out, int* status, int reps,
+                             float* best_ms);
+int ragged_class_split(const RaggedState* r, int64_t n);
+bool ragged_supported(int64_t n);
+
 // Per-translation-unit variant tables, gathered by the registry in api.cu.
 const RowsVariant* rows_variants_pow2(int* count);
 const RowsVariant* rows_variants_mixed(int* count);

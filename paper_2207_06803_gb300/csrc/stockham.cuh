@@ -67,9 +67,28 @@ struct StageTwiddles<L, R, Rest...> {
     static constexpr int value = (L > 1 ? (R - 1) * L : 0) + StageTwiddles<L * R, Rest...>::value;
 };
 
+// Row addressing of a tile: element n of tile row t.
+// ContigIO: rows are consecutive (row t at base + t*N).
+template <int N>
+struct ContigIO {
+    const float2* in;
+    float2* out;
+    __device__ __forceinline__ float2 ld(int t, int n) const { return in[t * N + n]; }
+    __device__ __forceinline__ void st(int t, int n, float2 v) const { out[t * N + n] = v; }
+};
+// IndexedIO: row t starts at complex element off[t] of both buffers (ragged batches).
+template <int N>
+struct IndexedIO {
+    const float2* in;
+    float2* out;
+    const long long* off;
+    __device__ __forceinline__ float2 ld(int t, int n) const { return in[off[t] + n]; }
+    __device__ __forceinline__ void st(int t, int n, float2 v) const { out[off[t] + n] = v; }
+};
+
 // Stage-1 operands of this thread's butterflies, straight from HBM.
-template <int N, int E, int T, int R>
-__device__ __forceinline__ void gather_global(float2 (&v)[E], const float2* gin, int nvalid) {
+template <int N, int E, int T, int R, class IO>
+__device__ __forceinline__ void gather_global(float2 (&v)[E], const IO& io, int nvalid) {
     constexpr int TPB = T * N / E, NB = E / R, NR = N / R;
     const int tid = threadIdx.x;
 #pragma unroll
@@ -77,8 +96,7 @@ __device__ __forceinline__ void gather_global(float2 (&v)[E], const float2* gin,
         const int B = tid + u * TPB;
         const int t = B / NR, j = B % NR;
 #pragma unroll
-        for (int q = 0; q < R; ++q)
-            v[u * R + q] = (t < nvalid) ? gin[t * N + j + q * NR] : make_float2(0.f, 0.f);
+        for (int q = 0; q < R; ++q) v[u * R + q] = (t < nvalid) ? io.ld(t, j + q * NR) : make_float2(0.f, 0.f);
     }
 }
 
@@ -99,8 +117,8 @@ __device__ __forceinline__ void gather_smem(float2 (&v)[E], const float2* sm) {
 // Stages from the one whose operands `v` already holds to the end.  SYNC0:
 // synchronise before the first shared-memory write (needed when earlier
 // readers of the tile buffer may still be running).
-template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest>
-__device__ __forceinline__ void run_stages(float2 (&v)[E], float2* gout, float2* sm, const float2* __restrict__ tw,
+template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest, class IO>
+__device__ __forceinline__ void run_stages(float2 (&v)[E], const IO& io, float2* sm, const float2* __restrict__ tw,
                                            int nvalid) {
     constexpr int TPB = T * N / E;
     constexpr int NB = E / R;  // butterflies per thread in this stage
@@ -127,7 +145,7 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* gout, float2*
             const int t = B / NR, j = B % NR;
             if (t < nvalid) {
 #pragma unroll
-                for (int q = 0; q < R; ++q) gout[t * N + q * L + j] = v[u * R + q];
+                for (int q = 0; q < R; ++q) io.st(t, q * L + j, v[u * R + q]);
             }
         }
     } else {
@@ -142,7 +160,7 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], float2* gout, float2*
         }
         __syncthreads();
         gather_smem<N, E, T, PS, First<Rest...>::value>(v, sm);
-        run_stages<N, S, E, T, PS, true, TWO + (L > 1 ? (R - 1) * L : 0), L * R, Rest...>(v, gout, sm, tw, nvalid);
+        run_stages<N, S, E, T, PS, true, TWO + (L > 1 ? (R - 1) * L : 0), L * R, Rest...>(v, io, sm, tw, nvalid);
     }
 }
 
@@ -160,8 +178,9 @@ __global__ void __launch_bounds__(T * N / E) k_stockham_rows(const float2* in, f
     const long long tile = blockIdx.x;
     const int nvalid = tile_rows(tile, T, batch);
     float2 v[E];
-    gather_global<N, E, T, First<Rs...>::value>(v, in + tile * T * N, nvalid);
-    run_stages<N, S, E, T, PS, false, 0, 1, Rs...>(v, out + tile * T * N, sm, tw, nvalid);
+    const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
+    gather_global<N, E, T, First<Rs...>::value>(v, io, nvalid);
+    run_stages<N, S, E, T, PS, false, 0, 1, Rs...>(v, io, sm, tw, nvalid);
 }
 
 // Persistent form with register prefetch of the next tile's stage-1 operands.
@@ -175,14 +194,17 @@ __global__ void __launch_bounds__(T * N / E) k_stockham_rows_pf(const float2* in
     const long long ntiles = (batch + T - 1) / T;
     long long tile = blockIdx.x;
     float2 nxt[E];
-    if (tile < ntiles) gather_global<N, E, T, R1>(nxt, in + tile * T * N, tile_rows(tile, T, batch));
+    if (tile < ntiles)
+        gather_global<N, E, T, R1>(nxt, ContigIO<N>{in + tile * T * N, nullptr}, tile_rows(tile, T, batch));
     for (; tile < ntiles; tile += gridDim.x) {
         float2 v[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = nxt[e];
         const long long next = tile + gridDim.x;
-        if (next < ntiles) gather_global<N, E, T, R1>(nxt, in + next * T * N, tile_rows(next, T, batch));
-        run_stages<N, S, E, T, PS, true, 0, 1, Rs...>(v, out + tile * T * N, sm, tw, tile_rows(tile, T, batch));
+        if (next < ntiles)
+            gather_global<N, E, T, R1>(nxt, ContigIO<N>{in + next * T * N, nullptr}, tile_rows(next, T, batch));
+        run_stages<N, S, E, T, PS, true, 0, 1, Rs...>(v, ContigIO<N>{nullptr, out + tile * T * N}, sm, tw,
+                                                      tile_rows(tile, T, batch));
     }
 }
 

@@ -62,6 +62,13 @@ PROTOTYPES = {
     "gbfft_variant_info": (_c_int, [_c_i64, _c_int, _c_intp, _c_intp, _c_intp, _c_intp, _c_intp]),
     "gbfft_plan_device_status": (_c_int, [_c_vp]),
     "gbfft_execute_twopass_noalloc": (_c_int, [_c_i64, _c_i64, _c_int, _c_vp, _c_vp, _c_vp]),
+    "gbfft_plan_ragged": (_c_int, [ctypes.POINTER(_c_vp), _c_i64p, _c_i64p, _c_i64, _c_int, _c_int]),
+    "gbfft_execute_ragged": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
+    "gbfft_ragged_autotune": (_c_int, [_c_vp, _c_vp, _c_vp, _c_int, ctypes.POINTER(ctypes.c_float)]),
+    "gbfft_ragged_num_items": (_c_i64, [_c_vp]),
+    "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
+    "gbfft_ragged_set_item_ready": (_c_int, [_c_vp, _c_i64, _c_int]),
+    "gbfft_ragged_set_wait_limit": (_c_int, [_c_vp, _c_i64]),
 }
 
 
@@ -199,6 +206,76 @@ def gbfft_execute_twopass_noalloc(n: int, batch: int, direction: int, x_in, x_ou
     library's static device array (see include/gbfft.h); allocates nothing."""
     _check(lib().gbfft_execute_twopass_noalloc(n, batch, direction, _ptr(x_in), _ptr(x_out), _stream(stream)),
            "gbfft_execute_twopass_noalloc")
+
+
+def gbfft_plan_ragged(n, offsets, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32) -> int:
+    """n, offsets: sequences of int64 (lengths and starting complex elements)."""
+    count = len(n)
+    an = (ctypes.c_int64 * count)(*[int(v) for v in n])
+    ao = (ctypes.c_int64 * count)(*[int(v) for v in offsets])
+    h = _c_vp()
+    _check(lib().gbfft_plan_ragged(ctypes.byref(h), an, ao, count, direction, dtype), "gbfft_plan_ragged")
+    return int(h.value)
+
+
+def gbfft_execute_ragged(plan: int, x_in, x_out, stream=None) -> None:
+    _check(lib().gbfft_execute_ragged(plan, _ptr(x_in), _ptr(x_out), _stream(stream)), "gbfft_execute_ragged")
+
+
+def gbfft_ragged_autotune(plan: int, x_in, x_out, reps: int = 5) -> float:
+    ms = ctypes.c_float()
+    _check(lib().gbfft_ragged_autotune(plan, _ptr(x_in), _ptr(x_out), reps, ctypes.byref(ms)),
+           "gbfft_ragged_autotune")
+    return float(ms.value)
+
+
+def gbfft_ragged_num_items(plan: int) -> int:
+    return int(lib().gbfft_ragged_num_items(plan))
+
+
+def gbfft_ragged_tile_split(plan: int, n: int) -> int:
+    return int(lib().gbfft_ragged_tile_split(plan, n))
+
+
+def gbfft_ragged_set_item_ready(plan: int, item: int, ready: int) -> None:
+    _check(lib().gbfft_ragged_set_item_ready(plan, item, ready), "gbfft_ragged_set_item_ready")
+
+
+def gbfft_ragged_set_wait_limit(plan: int, nanoseconds: int) -> None:
+    _check(lib().gbfft_ragged_set_wait_limit(plan, nanoseconds), "gbfft_ragged_set_wait_limit")
+
+
+class RaggedPlan:
+    """Owning wrapper of a ragged plan."""
+
+    def __init__(self, n, offsets, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32):
+        self.handle = gbfft_plan_ragged(n, offsets, direction, dtype)
+
+    def execute(self, x_in, x_out, stream=None) -> None:
+        gbfft_execute_ragged(self.handle, x_in, x_out, stream)
+
+    def autotune(self, x_in, x_out, reps: int = 5) -> float:
+        return gbfft_ragged_autotune(self.handle, x_in, x_out, reps)
+
+    def num_items(self) -> int:
+        return gbfft_ragged_num_items(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            gbfft_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:

@@ -1,0 +1,142 @@
+"""Ragged batches: one persistent launch (replayed from a CUDA graph) over
+transforms of 41 different lengths, checked transform by transform against
+the FP64 oracle; tile-shape autotuning; buffer patching; failure injection
+with a bounded wait."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import ncpu, row_rel_l2, tol_fp32
+from paper_2207_06803_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SEED = synth.DEFAULT_SEED
+
+
+def ragged_case(count, seed=SEED):
+    sizes = synth.ragged_sizes(seed, count)
+    offs = synth.ragged_offsets(sizes)
+    total = int(offs[-1] + sizes[-1])
+    flat = synth.uniform_flat(seed, 0, total)
+    return sizes, offs, flat
+
+
+def check_all(y_flat, x_flat, sizes, offs, direction=-1, skip=()):
+    """Every transform against the oracle, grouped by length."""
+    by_n = {}
+    for i, (n, o) in enumerate(zip(sizes.tolist(), offs.tolist())):
+        if i not in skip:
+            by_n.setdefault(n, []).append(o)
+    for n, starts in by_n.items():
+        idx = np.asarray(starts)[:, None] + np.arange(n)[None, :]
+        x = x_flat[idx].astype(np.complex128)
+        ref = oracle.dft(x, direction, nthreads=ncpu())
+        err = row_rel_l2(y_flat[idx], ref)
+        assert np.all(np.isfinite(err)), n
+        assert err.max() <= tol_fp32(n), f"n={n} max rel-L2 {err.max():.3e}"
+
+
+def run_plan(plan, flat, d_out=None):
+    import torch
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    if d_out is None:
+        d_out = torch.full_like(d_in, float("nan"))
+    plan.execute(d_in, d_out)
+    torch.cuda.synchronize()
+    return d_in, d_out
+
+
+def to_np(t):
+    return t.cpu().numpy().view(np.complex64)
+
+
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_ragged_10000_transforms_41_sizes(direction):
+    from paper_2207_06803_gb300 import gbfft
+    sizes, offs, flat = ragged_case(10000)
+    assert len(set(sizes.tolist())) == 41
+    with gbfft.RaggedPlan(sizes, offs, direction) as p:
+        assert p.num_items() > 0
+        _, d_out = run_plan(p, flat)
+        assert gbfft.gbfft_plan_device_status(p.handle) == 0
+        y = to_np(d_out)
+    check_all(y, flat, sizes, offs, direction)
+
+
+def test_ragged_in_place_and_buffer_patching():
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    sizes, offs, flat = ragged_case(600, seed=SEED + 1)
+    with gbfft.RaggedPlan(sizes, offs) as p:
+        d_in, d_out = run_plan(p, flat)                 # captures the graph on (d_in, d_out)
+        ref = d_out.clone()
+        d_in2 = d_in.clone()
+        d_out2 = torch.zeros_like(d_in)
+        p.execute(d_in2, d_out2)                        # patched kernel-node parameters
+        p.execute(d_in2, d_in2)                         # in place, patched again
+        torch.cuda.synchronize()
+        assert torch.equal(d_out2, ref)
+        assert torch.equal(d_in2, ref)
+    check_all(to_np(ref), flat, sizes, offs)
+
+
+def test_autotuned_shapes_give_identical_results():
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    sizes, offs, flat = ragged_case(3000, seed=SEED + 2)
+    with gbfft.RaggedPlan(sizes, offs) as p:
+        d_in, d_out = run_plan(p, flat)
+        before = d_out.clone()
+        ms = p.autotune(d_in, d_out, reps=3)
+        assert ms > 0
+        splits = {n: gbfft.gbfft_ragged_tile_split(p.handle, n) for n in set(sizes.tolist())}
+        assert set(splits.values()) <= {1, 2, 4, 8}
+        d_out.fill_(float("nan"))
+        p.execute(d_in, d_out)
+        torch.cuda.synchronize()
+        assert torch.equal(d_out, before)
+
+
+def test_not_ready_item_times_out_and_is_skipped():
+    """Failure injection on the host: one queue item is never published.  The
+    kernel's bounded wait expires, the status word reads TIMEOUT, that item's
+    rows keep the canary, every other transform is still correct, and the plan
+    works again once the item is ready."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    sizes, offs, flat = ragged_case(400, seed=SEED + 3)
+    with gbfft.RaggedPlan(sizes, offs) as p:
+        gbfft.gbfft_ragged_set_wait_limit(p.handle, 20_000_000)  # 20 ms
+        gbfft.gbfft_ragged_set_item_ready(p.handle, 0, 0)
+        d_in, d_out = run_plan(p, flat)
+        assert gbfft.gbfft_plan_device_status(p.handle) == gbfft.GBFFT_ERR_TIMEOUT
+        y = to_np(d_out)
+        untouched = [i for i, (n, o) in enumerate(zip(sizes, offs)) if np.all(np.isnan(y[o:o + n]))]
+        assert 1 <= len(untouched) <= 256  # exactly the rows of one item: one length, at most one tile
+        assert all(sizes[i] == sizes[untouched[0]] for i in untouched)
+        check_all(y, flat, sizes, offs, skip=set(untouched))
+        gbfft.gbfft_ragged_set_item_ready(p.handle, 0, 1)
+        d_out.fill_(float("nan"))
+        p.execute(d_in, d_out)
+        torch.cuda.synchronize()
+        assert gbfft.gbfft_plan_device_status(p.handle) == 0
+        check_all(to_np(d_out), flat, sizes, offs)
+
+
+def test_ragged_errors():
+    from paper_2207_06803_gb300 import gbfft
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_ragged([8, 11], [0, 8])
+    assert e.value.status == gbfft.GBFFT_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_ragged([16, 16], [0, 8])
+    assert e.value.status == gbfft.GBFFT_ERR_OVERLAP
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_ragged([16], [-1])
+    assert e.value.status == gbfft.GBFFT_ERR_INVALID_ARG
+    with gbfft.RaggedPlan([16, 8192], [0, 16]) as p:
+        with pytest.raises(gbfft.GbfftError):
+            gbfft.gbfft_execute(p.handle, 0, 0)
+        with pytest.raises(gbfft.GbfftError) as e:
+            gbfft.gbfft_ragged_set_item_ready(p.handle, 99, 1)
+        assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
