@@ -57,7 +57,9 @@ typedef enum {
 #define GBFFT_INVERSE (+1)
 
 typedef enum {
-    GBFFT_C2C_F32 = 0 /* complex64 in/out, FP32 arithmetic, FP64-generated twiddles */
+    GBFFT_C2C_F32 = 0,           /* complex64 in/out, FP32 arithmetic, FP64-generated twiddles */
+    GBFFT_C2C_F32_TC_FP16X2 = 1, /* complex64 in/out; every DFT_16 block as FP16 hi+lo tensor-core products */
+    GBFFT_C2C_F32_TC_BF16X2 = 2  /* complex64 in/out; every DFT_16 block as BF16 hi+lo tensor-core products */
 } gbfft_dtype;
 
 /* Human-readable name of a status code (static storage; never NULL). */
@@ -74,6 +76,14 @@ int gbfft_version(void);
  * float32.  batch may be 0 (execute is then a no-op).  On success *out holds a
  * new plan that the caller releases with gbfft_destroy().  Errors:
  * INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.  *out is set to NULL on error.
+ *
+ * Tensor-core dtypes (GBFFT_C2C_F32_TC_*): n must be 16, 256 or 4096 (an
+ * all-radix-16 schedule).  Each stage's DFT_16 - the dense DFT(16) block of
+ * the factorisation (Table I), multiplied as a matrix - runs as a 32x32 real
+ * product on the tensor cores with both operands split into high and low
+ * half-precision parts (Mh Xh + Mh Xl + Ml Xh, FP32 accumulation); FP16
+ * columns are scaled by exact powers of two first.  Stage twiddles stay FP32.
+ * The variant and two-pass forms are FP32-only (INVALID_ARG otherwise).
  */
 gbfft_status gbfft_plan_create(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype);
 

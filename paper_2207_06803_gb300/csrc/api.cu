@@ -57,7 +57,7 @@ cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, f
 
 using namespace gbfft;
 
-enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1, kPlanRagged = 2 };
+enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1, kPlanRagged = 2, kPlanTensorCore = 3 };
 
 struct gbfft_plan_s {
     int64_t n = 0;
@@ -81,6 +81,10 @@ struct gbfft_plan_s {
     float2* ws = nullptr;    // workspace z, batch * n complex
     // ragged batch
     RaggedState* ragged = nullptr;
+    // tensor-core split precision (all-radix-16 schedule)
+    const TcVariant* tcv = nullptr;
+    int tc_prec = 0;
+    uint32_t* tc_frag = nullptr;
     int* status = nullptr;
     size_t ws_bytes = 0;
     // host-buffer execution: staging ring and its streams/events (created on first use)
@@ -121,6 +125,7 @@ void free_plan(gbfft_plan p) {
     if (p->s_in) cudaStreamDestroy(p->s_in);
     if (p->s_out) cudaStreamDestroy(p->s_out);
     if (p->ragged) ragged_destroy(p->ragged);
+    if (p->tc_frag) cudaFree(p->tc_frag);
     float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
     for (float2* b : bufs)
         if (b) cudaFree(b);
@@ -160,13 +165,51 @@ gbfft_status alloc_stage_tables(float2** dst, int64_t n, const int* radix, int n
     return launch_stage_twiddles(*dst, n, radix, nstages, 0) == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
+gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype) {
+    const TcVariant* tv = tc_variant_for(n);
+    if (!tv) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    gbfft_plan p = new (std::nothrow) gbfft_plan_s();
+    if (!p) return GBFFT_ERR_OOM;
+    p->kind = kPlanTensorCore;
+    p->n = n;
+    p->batch = batch;
+    p->direction = direction;
+    p->dtype = dtype;
+    p->tcv = tv;
+    p->tc_prec = dtype == GBFFT_C2C_F32_TC_FP16X2 ? 0 : 1;
+    int radix[kMaxStages];
+    for (int s = 0; s < tv->nstages; ++s) radix[s] = 16;
+    gbfft_status st = GBFFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess || cudaMalloc(&p->tc_frag, 32 * 32 * 4) != cudaSuccess) {
+        cudaGetLastError();
+        st = GBFFT_ERR_OOM;
+    }
+    if (st == GBFFT_OK && prepare_tc(*tv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw, n, radix, tv->nstages);
+    if (st == GBFFT_OK && launch_tc_fragments(p->tc_frag, p->tc_prec, direction, 0) != cudaSuccess)
+        st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st != GBFFT_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return GBFFT_OK;
+}
+
 gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int variant,
                     int64_t k_outer) {
     if (!out) return GBFFT_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 1 || batch < 0 || k_outer < 0) return GBFFT_ERR_INVALID_ARG;
     if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
-    if (dtype != GBFFT_C2C_F32) return GBFFT_ERR_INVALID_ARG;
+    if (dtype != GBFFT_C2C_F32 && dtype != GBFFT_C2C_F32_TC_FP16X2 && dtype != GBFFT_C2C_F32_TC_BF16X2)
+        return GBFFT_ERR_INVALID_ARG;
+    if (dtype != GBFFT_C2C_F32) {
+        if (variant >= 0 || k_outer > 0) return GBFFT_ERR_INVALID_ARG;
+        return create_tc(out, n, batch, direction, dtype);
+    }
 
     const RowsVariant* cands[kMaxVariantsPerSize];
     const int nc = rows_variants_for(n, cands, kMaxVariantsPerSize);
@@ -234,6 +277,8 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
 
 // Enqueue the transform of `rows` rows from `in` to `out` (device pointers).
 cudaError_t run_device(gbfft_plan p, const float2* in, float2* out, int64_t rows, cudaStream_t s) {
+    if (p->kind == kPlanTensorCore)
+        return launch_tc(*p->tcv, p->tc_prec, p->direction, in, out, p->tw, p->tc_frag, (long long)rows, s);
     if (p->kind == kPlanSingle)
         return launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)rows, p->grid_cap, s);
     cudaError_t e = launch_cols(*p->cv_m, 1, p->direction, in, p->ws, p->tw_m, p->post, (long long)rows,
@@ -377,6 +422,8 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     int rad[2 * kMaxStages];
     if (p->kind == kPlanRagged) {
         // no single schedule: one per length class
+    } else if (p->kind == kPlanTensorCore) {
+        for (int i = 0; i < p->tcv->nstages; ++i) rad[ns++] = 16;
     } else if (p->kind == kPlanSingle) {
         for (int i = 0; i < p->rv->nstages; ++i) rad[ns++] = p->rv->radix[i];
     } else {
@@ -393,8 +440,9 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
 
 gbfft_status gbfft_plan_factors(gbfft_plan p, int64_t* k_outer, int64_t* m_inner) {
     if (!p || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
-    if (k_outer) *k_outer = p->kind == kPlanSingle ? 1 : p->k_outer;
-    if (m_inner) *m_inner = p->kind == kPlanSingle ? p->n : p->m_inner;
+    const bool one = p->kind != kPlanTwoPass;
+    if (k_outer) *k_outer = one ? 1 : p->k_outer;
+    if (m_inner) *m_inner = one ? p->n : p->m_inner;
     return GBFFT_OK;
 }
 

@@ -58,6 +58,20 @@ cudaError_t launch_cols(const ColsVariant& v, int pass, int direction, const flo
 // D^N_M table in workspace layout: post[k*M + j1] = w_N^(j1*k), k < N/M, j1 < M.
 cudaError_t launch_post_twiddles(float2* post, int64_t n, int64_t m, cudaStream_t stream);
 
+// Tensor-core variant (tc.cu): all-radix-16 schedules, DFT_16 as split
+// half-precision mma products.  k[prec][dir]: prec 0 = FP16x2, 1 = BF16x2;
+// dir 0 = forward, 1 = inverse.
+struct TcVariant {
+    int n, rows, tpb, nstages, smem;
+    const void* k[2][2];
+};
+const TcVariant* tc_variant_for(int64_t n);
+cudaError_t prepare_tc(const TcVariant& v);
+// frag: 32 lanes x 32 words; prec as above; sign = exponent sign of the transform.
+cudaError_t launch_tc_fragments(uint32_t* frag, int prec, int sign, cudaStream_t s);
+cudaError_t launch_tc(const TcVariant& v, int prec, int direction, const float2* in, float2* out, const float2* tw,
+                      const uint32_t* frag, long long batch, cudaStream_t s);
+
 // Ragged-batch plans (ragged.cu).
 struct RaggedState;
 gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* offsets, int64_t count);

@@ -22,6 +22,8 @@ LIB_PATH = os.path.join(_HERE, "libgbfft.so")
 GBFFT_FORWARD = -1
 GBFFT_INVERSE = +1
 GBFFT_C2C_F32 = 0
+GBFFT_C2C_F32_TC_FP16X2 = 1
+GBFFT_C2C_F32_TC_BF16X2 = 2
 
 STATUS_NAMES = {
     0: "GBFFT_OK",

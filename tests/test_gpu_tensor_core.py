@@ -1,0 +1,93 @@
+"""Tensor-core split-precision variant (FP16x2 with exact power-of-two column
+scaling, BF16x2): relative L2 error against the FP64 oracle within
+1e-6*log2(N), per size, direction and input distribution, and the error
+actually achieved recorded per case."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import TC_TOL_PER_LOG2N, ncpu, row_rel_l2
+from paper_2207_06803_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+SEED = synth.DEFAULT_SEED
+DTYPES = {"fp16x2": 1, "bf16x2": 2}
+
+
+def inputs(dist, n, batch):
+    if dist == "uniform":
+        return synth.uniform_batch(SEED + n, n, batch)
+    return synth.gaussian_scaled_batch(SEED + n, n, batch)
+
+
+def run_tc(x, direction, dtype):
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    batch, n = x.shape
+    d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.float32).reshape(-1)).cuda()
+    d_out = torch.empty_like(d_in)
+    with gbfft.Plan(n, batch, direction, dtype) as p:
+        assert p.info()["radices"] == [16] * int(round(math.log(n, 16)))
+        p.execute(d_in, d_out)
+        torch.cuda.synchronize()
+    return d_out.cpu().numpy().view(np.complex64).reshape(batch, n)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "gaussian_scaled"])
+@pytest.mark.parametrize("dtype", list(DTYPES))
+@pytest.mark.parametrize("direction", [-1, 1])
+@pytest.mark.parametrize("n,batch", [(16, 4099), (256, 515), (4096, 67)])
+def test_tensor_core_error_within_gate(n, batch, direction, dtype, dist):
+    x = inputs(dist, n, batch)
+    y = run_tc(x, direction, DTYPES[dtype])
+    ref = oracle.dft(x.astype(np.complex128), direction, nthreads=ncpu())
+    err = row_rel_l2(y, ref)
+    gate = TC_TOL_PER_LOG2N * math.log2(n)
+    assert np.all(np.isfinite(err))
+    assert err.max() <= gate, f"{dtype} {dist} n={n}: max {err.max():.3e} > {gate:.3e}"
+
+
+@pytest.mark.parametrize("dtype", list(DTYPES))
+@pytest.mark.parametrize("n,batch", [(256, 1 << 18), (4096, 1 << 14)])
+def test_tensor_core_config_sizes_sampled(n, batch, dtype):
+    """The full tensor-core configuration (2^26 points), 512 sampled rows."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    x = synth.gaussian_scaled_batch(SEED, n, batch)
+    d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+    d_out = torch.empty_like(d_in)
+    with gbfft.Plan(n, batch, -1, DTYPES[dtype]) as p:
+        p.execute(d_in, d_out)
+        torch.cuda.synchronize()
+    rows = synth.sample_rows(SEED + n, batch, 512)
+    y = d_out.view(batch, 2 * n).index_select(0, torch.from_numpy(rows).cuda()).cpu().numpy().view(np.complex64)
+    ref = oracle.dft(x[rows].astype(np.complex128), -1, nthreads=ncpu())
+    assert row_rel_l2(y, ref).max() <= TC_TOL_PER_LOG2N * math.log2(n)
+
+
+def test_tensor_core_rejects_other_sizes_and_forms():
+    from paper_2207_06803_gb300 import gbfft
+    for n in (8, 512, 1024, 8192):
+        with pytest.raises(gbfft.GbfftError) as e:
+            gbfft.gbfft_plan_create(n, 4, -1, 1)
+        assert e.value.status == gbfft.GBFFT_ERR_UNSUPPORTED_SIZE
+    with pytest.raises(gbfft.GbfftError):
+        gbfft.gbfft_plan_create_variant(256, 4, -1, 1, 0)
+
+
+def test_tensor_core_in_place_and_host_pipeline():
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    x = synth.uniform_batch(SEED, 256, 9000)
+    d = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+    ref = torch.empty_like(d)
+    h_in = d.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    with gbfft.Plan(256, 9000, -1, 2) as p:
+        p.execute(d, ref)
+        p.execute_host(h_in, h_out)
+        p.execute(d, d)
+        torch.cuda.synchronize()
+    assert torch.equal(d, ref) and torch.equal(h_out, ref.cpu())
