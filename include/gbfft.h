@@ -78,7 +78,9 @@ int gbfft_version(void);
  * INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.  *out is set to NULL on error.
  *
  * Tensor-core dtypes (GBFFT_C2C_F32_TC_*): n must be 16, 256 or 4096 (an
- * all-radix-16 schedule).  Each stage's DFT_16 - the dense DFT(16) block of
+ * all-radix-16 schedule; BF16x2 only 256 and 4096, because its single-stage
+ * error at 16, about 5e-6 relative L2, exceeds the 1e-6*log2(N) accuracy
+ * contract of the tensor-core path).  Each stage's DFT_16 - the dense DFT(16) block of
  * the factorisation (Table I), multiplied as a matrix - runs as a 32x32 real
  * product on the tensor cores with both operands split into high and low
  * half-precision parts (Mh Xh + Mh Xl + Ml Xh, FP32 accumulation); FP16
@@ -225,6 +227,57 @@ int gbfft_ragged_tile_split(gbfft_plan p, int64_t n);
  */
 gbfft_status gbfft_ragged_set_item_ready(gbfft_plan p, int64_t item, int ready);
 gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
+
+/*
+ * Serving loop (native, one worker thread per server): continuous batching of
+ * FFT requests under a device-memory budget.
+ *
+ * gbfft_server_create: `mem_budget_bytes` of device memory is reserved once
+ * (one cudaMalloc) as the arena every admitted request's slot comes from;
+ * `n_streams` (1..64) streams carry the groups; flags GBFFT_SERVER_SERIAL
+ * turns batching off (one request in flight, one stream: the naive queue).
+ * gbfft_server_submit queues a request - `batch` rows of length n (any length
+ * gbfft_plan_create supports), direction, HOST input and output buffers of
+ * 8*n*batch bytes each (page-locked for overlap; they must stay valid until
+ * the request completes) - stamps its arrival time and returns a ticket.
+ * BUDGET if the request alone exceeds the arena, UNSUPPORTED_SIZE for lengths
+ * with no plan.  The worker admits queued requests in FIFO order while their
+ * slots fit in the arena, groups the admitted ones by (n, direction) into one
+ * contiguous slot and one transform launch each, on the next stream of the
+ * pool: requests arriving while earlier groups run are admitted as memory
+ * frees up and overlap them.  Schedules and twiddle tables are built once per
+ * (n, direction) and stay resident (gbfft_server_prepare builds them ahead).
+ * A host callback after each group's copies back stamps completion; latency
+ * is completion - arrival.
+ * gbfft_server_poll: *done = 1 finished, 0 pending, -1 failed/cancelled;
+ * *latency_s once finished.  gbfft_server_wait blocks up to timeout_s
+ * (TIMEOUT otherwise).  gbfft_server_release forgets a finished ticket.
+ * gbfft_server_replay submits `count` requests at arrival offsets arrival_s[i]
+ * (seconds after the call, non-decreasing) from the calling thread - an open
+ * loop generator - and returns their tickets.
+ * gbfft_server_stats fills out10 = {completed, p50 latency s, p99 latency s,
+ * max latency s, requests/s, GB/s (16*n*batch bytes per request), groups
+ * launched, max requests in flight, max arena bytes in use, window s}; the
+ * window runs from the last reset/replay to the last completion.
+ * gbfft_server_destroy cancels queued requests, waits for running ones and
+ * frees everything.
+ */
+typedef struct gbfft_server_s *gbfft_server;
+#define GBFFT_SERVER_SERIAL 1
+
+gbfft_status gbfft_server_create(gbfft_server *out, size_t mem_budget_bytes, int n_streams, int flags);
+gbfft_status gbfft_server_prepare(gbfft_server srv, int64_t n, int direction);
+gbfft_status gbfft_server_submit(gbfft_server srv, int64_t n, int64_t batch, int direction, const void *host_in,
+                                 void *host_out, uint64_t *ticket);
+gbfft_status gbfft_server_poll(gbfft_server srv, uint64_t ticket, int *done, double *latency_s);
+gbfft_status gbfft_server_wait(gbfft_server srv, uint64_t ticket, double timeout_s);
+gbfft_status gbfft_server_release(gbfft_server srv, uint64_t ticket);
+gbfft_status gbfft_server_replay(gbfft_server srv, int64_t count, const int64_t *n, const int64_t *batch,
+                                 const int *direction, const void *const *host_in, void *const *host_out,
+                                 const double *arrival_s, uint64_t *tickets);
+gbfft_status gbfft_server_stats(gbfft_server srv, double *out10);
+gbfft_status gbfft_server_reset_stats(gbfft_server srv);
+gbfft_status gbfft_server_destroy(gbfft_server srv);
 
 /*
  * Allocation-free two-pass transform (the paper has no counterpart: this is

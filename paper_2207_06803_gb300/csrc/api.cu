@@ -168,6 +168,9 @@ gbfft_status alloc_stage_tables(float2** dst, int64_t n, const int* radix, int n
 gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype) {
     const TcVariant* tv = tc_variant_for(n);
     if (!tv) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    // BF16x2 keeps ~17 significand bits; a lone radix-16 stage then errs by ~5e-6
+    // relative L2, above the 1e-6*log2(N) = 4e-6 contract at N = 16.
+    if (dtype == GBFFT_C2C_F32_TC_BF16X2 && n < 256) return GBFFT_ERR_UNSUPPORTED_SIZE;
     gbfft_plan p = new (std::nothrow) gbfft_plan_s();
     if (!p) return GBFFT_ERR_OOM;
     p->kind = kPlanTensorCore;

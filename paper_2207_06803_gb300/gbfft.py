@@ -71,7 +71,23 @@ PROTOTYPES = {
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
     "gbfft_ragged_set_item_ready": (_c_int, [_c_vp, _c_i64, _c_int]),
     "gbfft_ragged_set_wait_limit": (_c_int, [_c_vp, _c_i64]),
+    "gbfft_server_create": (_c_int, [ctypes.POINTER(_c_vp), _c_size, _c_int, _c_int]),
+    "gbfft_server_prepare": (_c_int, [_c_vp, _c_i64, _c_int]),
+    "gbfft_server_submit": (_c_int, [_c_vp, _c_i64, _c_i64, _c_int, _c_vp, _c_vp,
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "gbfft_server_poll": (_c_int, [_c_vp, ctypes.c_uint64, _c_intp, ctypes.POINTER(ctypes.c_double)]),
+    "gbfft_server_wait": (_c_int, [_c_vp, ctypes.c_uint64, ctypes.c_double]),
+    "gbfft_server_release": (_c_int, [_c_vp, ctypes.c_uint64]),
+    "gbfft_server_replay": (_c_int, [_c_vp, _c_i64, _c_i64p, _c_i64p, _c_intp, ctypes.POINTER(_c_vp),
+                                     ctypes.POINTER(_c_vp), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_uint64)]),
+    "gbfft_server_stats": (_c_int, [_c_vp, ctypes.POINTER(ctypes.c_double)]),
+    "gbfft_server_reset_stats": (_c_int, [_c_vp]),
+    "gbfft_server_destroy": (_c_int, [_c_vp]),
 }
+GBFFT_SERVER_SERIAL = 1
+SERVER_STATS = ("completed", "p50_s", "p99_s", "max_s", "req_per_s", "gb_per_s", "groups",
+                "max_inflight_requests", "max_arena_bytes", "window_s")
 
 
 class GbfftError(RuntimeError):
@@ -265,6 +281,118 @@ class RaggedPlan:
     def close(self) -> None:
         if getattr(self, "handle", None):
             gbfft_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _hptr(x) -> int:
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    return _ptr(x)
+
+
+def gbfft_server_create(mem_budget_bytes: int, n_streams: int = 4, flags: int = 0) -> int:
+    h = _c_vp()
+    _check(lib().gbfft_server_create(ctypes.byref(h), mem_budget_bytes, n_streams, flags), "gbfft_server_create")
+    return int(h.value)
+
+
+def gbfft_server_prepare(srv: int, n: int, direction: int = GBFFT_FORWARD) -> None:
+    _check(lib().gbfft_server_prepare(srv, n, direction), "gbfft_server_prepare")
+
+
+def gbfft_server_submit(srv: int, n: int, batch: int, direction: int, host_in, host_out) -> int:
+    t = ctypes.c_uint64()
+    _check(lib().gbfft_server_submit(srv, n, batch, direction, _hptr(host_in), _hptr(host_out), ctypes.byref(t)),
+           "gbfft_server_submit")
+    return int(t.value)
+
+
+def gbfft_server_poll(srv: int, ticket: int) -> tuple[int, float]:
+    done, lat = ctypes.c_int(), ctypes.c_double()
+    _check(lib().gbfft_server_poll(srv, ticket, ctypes.byref(done), ctypes.byref(lat)), "gbfft_server_poll")
+    return done.value, lat.value
+
+
+def gbfft_server_wait(srv: int, ticket: int, timeout_s: float = 60.0) -> None:
+    _check(lib().gbfft_server_wait(srv, ticket, timeout_s), "gbfft_server_wait")
+
+
+def gbfft_server_release(srv: int, ticket: int) -> None:
+    _check(lib().gbfft_server_release(srv, ticket), "gbfft_server_release")
+
+
+def gbfft_server_replay(srv: int, n, batch, direction, host_in, host_out, arrival_s) -> list[int]:
+    cnt = len(n)
+    an = (ctypes.c_int64 * cnt)(*[int(v) for v in n])
+    ab = (ctypes.c_int64 * cnt)(*[int(v) for v in batch])
+    ad = (ctypes.c_int * cnt)(*[int(v) for v in direction])
+    ai = (_c_vp * cnt)(*[_hptr(v) for v in host_in])
+    ao = (_c_vp * cnt)(*[_hptr(v) for v in host_out])
+    at = (ctypes.c_double * cnt)(*[float(v) for v in arrival_s])
+    tk = (ctypes.c_uint64 * cnt)()
+    _check(lib().gbfft_server_replay(srv, cnt, an, ab, ad, ai, ao, at, tk), "gbfft_server_replay")
+    return [int(v) for v in tk]
+
+
+def gbfft_server_stats(srv: int) -> dict:
+    out = (ctypes.c_double * 10)()
+    _check(lib().gbfft_server_stats(srv, out), "gbfft_server_stats")
+    return dict(zip(SERVER_STATS, list(out)))
+
+
+def gbfft_server_reset_stats(srv: int) -> None:
+    _check(lib().gbfft_server_reset_stats(srv), "gbfft_server_reset_stats")
+
+
+def gbfft_server_destroy(srv: int) -> None:
+    _check(lib().gbfft_server_destroy(srv), "gbfft_server_destroy")
+
+
+class Server:
+    """Continuous-batching FFT server (see include/gbfft.h); host buffers in/out."""
+
+    def __init__(self, mem_budget_bytes: int = 4 << 30, n_streams: int = 4, serial: bool = False):
+        self.handle = gbfft_server_create(mem_budget_bytes, n_streams, GBFFT_SERVER_SERIAL if serial else 0)
+
+    def prepare(self, n: int, direction: int = GBFFT_FORWARD) -> None:
+        gbfft_server_prepare(self.handle, n, direction)
+
+    def submit(self, n: int, batch: int, direction: int, host_in, host_out) -> int:
+        return gbfft_server_submit(self.handle, n, batch, direction, host_in, host_out)
+
+    def poll(self, ticket: int) -> tuple[int, float]:
+        return gbfft_server_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
+        gbfft_server_wait(self.handle, ticket, timeout_s)
+
+    def release(self, ticket: int) -> None:
+        gbfft_server_release(self.handle, ticket)
+
+    def replay(self, n, batch, direction, host_in, host_out, arrival_s) -> list[int]:
+        return gbfft_server_replay(self.handle, n, batch, direction, host_in, host_out, arrival_s)
+
+    def stats(self) -> dict:
+        return gbfft_server_stats(self.handle)
+
+    def reset_stats(self) -> None:
+        gbfft_server_reset_stats(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            lib().gbfft_server_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):
