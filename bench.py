@@ -53,12 +53,16 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
+    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving"], default="sweep",
+                    help="sweep (default, the headline line) or one of the other configurations")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sizes", type=str, default=None,
                     help="comma-separated subset of the sweep (for small profiling cases)")
+    ap.add_argument("--dtype", type=int, default=0,
+                    help="plan dtype for the sweep runner (0 FP32, 1 FP16x2 and 2 BF16x2 tensor-core; profiling)")
     ap.add_argument("--points-log2", type=int, default=26,
                     help="complex points per call (default 26: the 512 MiB sweep workload)")
     args = ap.parse_args()
@@ -298,7 +302,7 @@ def run_gpu(args):
     plans = []
     for n in SWEEP:
         for direction in (gbfft.GBFFT_FORWARD, gbfft.GBFFT_INVERSE):
-            plans.append(((n, direction), gbfft.Plan(n, TOTAL // n, direction)))
+            plans.append(((n, direction), gbfft.Plan(n, TOTAL // n, direction, args.dtype)))
     calls = len(plans)
 
     def step(events=None):
@@ -434,10 +438,227 @@ def run_e2e(torch, np, flat, plans, stream, world, e2e_steps, calls):
             "path": "gbfft_execute_host (pinned host buffers, 32 MiB chunk ring)"}
 
 
+# --------------------------------------------------------------------------
+# Other configurations (one JSON line each; not the headline line)
+# --------------------------------------------------------------------------
+
+def _time_ms(torch, fn, reps, stream):
+    """Median CUDA-event time of fn() over reps runs on `stream` (after 3 warm-ups)."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def _peak():
+    peaks, src = measured_peaks()
+    return float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)), src
+
+
+def run_twopass(args):
+    """Eq. 2 two-pass lengths 5120..16384 at 2^26 points per call."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    flat = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL)
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    d_out = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    peak, src = _peak()
+    rows = {}
+    for n in (5120, 6144, 7168, 8192, 10240, 12288, 14336, 16384, 65536):
+        with gbfft.Plan(n, TOTAL // n, -1) as p:
+            info = p.info()
+            ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+        alg = BYTES_PER_CALL / (ms * 1e-3) / 1e9
+        rows[str(n)] = {"k_outer": info["k_outer"], "m_inner": info["m_inner"], "ms": ms, "alg_gbs": alg,
+                        "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak}
+    print(json.dumps({"config": "twopass", "metric": "two-pass Eq. 2 c2c GB/s (16 B/point algorithmic)",
+                      "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src,
+                      "per_size": rows}), flush=True)
+    return 0
+
+
+def run_tc(args):
+    """Tensor-core split precision vs the plain FP32 kernel: N=256 (2^18 rows), N=4096 (2^14 rows)."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peak, src = _peak()
+    out = {}
+    for n, dist in ((256, "uniform"), (4096, "uniform"), (256, "gaussian_scaled"), (4096, "gaussian_scaled")):
+        batch = TOTAL // n
+        x = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL) if dist == "uniform" else \
+            synth.gaussian_scaled_batch(synth.DEFAULT_SEED, n, batch).reshape(-1)
+        d_in = torch.from_numpy(x.view(np.float32)).cuda()
+        d_out = torch.empty_like(d_in)
+        d_rt = torch.empty_like(d_in)
+        for name, dt in (("fp32", 0), ("fp16x2", 1), ("bf16x2", 2)):
+            with gbfft.Plan(n, batch, -1, dt) as pf, gbfft.Plan(n, batch, 1, dt) as pi:
+                ms = _time_ms(torch, lambda: pf.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+                pi.execute(d_out, d_rt, stream)
+                torch.cuda.synchronize()
+            xr = d_in.view(batch, 2 * n)[:4096].double()
+            rr = d_rt.view(batch, 2 * n)[:4096].double()
+            rt = (torch.linalg.vector_norm(rr - n * xr, dim=1) / torch.linalg.vector_norm(n * xr, dim=1)).max()
+            gbs = BYTES_PER_CALL / (ms * 1e-3) / 1e9
+            out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak,
+                                         "roundtrip_rel_l2_max": float(rt)}
+    for key in list(out):
+        n, dist, name = key.split("/")
+        out[key]["vs_fp32"] = out[key]["gbs"] / out[f"{n}/{dist}/fp32"]["gbs"]
+    print(json.dumps({"config": "tc", "metric": "tensor-core split-precision c2c GB/s vs plain FP32",
+                      "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src,
+                      "results": out}), flush=True)
+    return 0
+
+
+def run_ragged(args):
+    """10,000 transforms over the 41 lengths {2^k,3*2^k,5*2^k,7*2^k} in [8, 8192]: one persistent
+    launch from a CUDA graph (autotuned tile shapes) vs one launch per length (grouped layout) vs one
+    launch per transform."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sizes = synth.ragged_sizes(synth.DEFAULT_SEED, 10000)
+    offs = synth.ragged_offsets(sizes)
+    total = int(offs[-1] + sizes[-1])
+    flat = synth.uniform_flat(synth.DEFAULT_SEED, 0, total)
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    d_out = torch.empty_like(d_in)
+    nbytes = 16.0 * total
+    reps = max(20, args.steps // 5)
+    res = {"transforms": int(sizes.size), "distinct_sizes": int(len(set(sizes.tolist()))),
+           "points": total, "algorithmic_bytes": nbytes}
+    with gbfft.RaggedPlan(sizes, offs, -1) as rp:
+        ms0 = _time_ms(torch, lambda: rp.execute(d_in, d_out, stream), reps, stream)
+        tuned = rp.autotune(d_in, d_out, reps=5)
+        ms1 = _time_ms(torch, lambda: rp.execute(d_in, d_out, stream), reps, stream)
+        res["ragged_graph_default_us"] = 1e3 * ms0
+        res["ragged_graph_tuned_us"] = 1e3 * ms1
+        res["ragged_gbs"] = nbytes / (ms1 * 1e-3) / 1e9
+        res["items"] = rp.num_items()
+        res["tile_splits"] = {str(n): gbfft.gbfft_ragged_tile_split(rp.handle, int(n))
+                              for n in sorted(set(sizes.tolist()))}
+    # (i) one launch per distinct length over a grouped copy of the data
+    order = np.argsort(sizes, kind="stable")
+    grouped = np.concatenate([flat[offs[i]:offs[i] + sizes[i]] for i in order])
+    g_in = torch.from_numpy(grouped.view(np.float32)).cuda()
+    g_out = torch.empty_like(g_in)
+    plans, start = [], 0
+    for n in sorted(set(sizes.tolist())):
+        cnt = int((sizes == n).sum())
+        plans.append((gbfft.Plan(n, cnt, -1), 2 * start, 2 * (start + n * cnt)))
+        start += n * cnt
+
+    def per_size():
+        for p, a, b in plans:
+            p.execute(g_in[a:b], g_out[a:b], stream)
+    ms2 = _time_ms(torch, per_size, reps, stream)
+    res["per_size_launches"] = len(plans)
+    res["per_size_us"] = 1e3 * ms2
+    res["per_size_gbs"] = nbytes / (ms2 * 1e-3) / 1e9
+    for p, _, _ in plans:
+        p.close()
+    # (ii) one launch per transform
+    single = {n: gbfft.Plan(int(n), 1, -1) for n in set(sizes.tolist())}
+    ptr_in, ptr_out = d_in.data_ptr(), d_out.data_ptr()
+    calls = [(single[int(n)].handle, ptr_in + 8 * int(o), ptr_out + 8 * int(o)) for n, o in zip(sizes, offs)]
+    sh = stream.cuda_stream
+
+    def per_transform():
+        for h, a, b in calls:
+            gbfft.gbfft_execute(h, a, b, sh)
+    ms3 = _time_ms(torch, per_transform, 5, stream)
+    res["per_transform_launches"] = len(calls)
+    res["per_transform_us"] = 1e3 * ms3
+    res["per_transform_gbs"] = nbytes / (ms3 * 1e-3) / 1e9
+    for p in single.values():
+        p.close()
+    res["speedup_vs_per_size"] = ms2 / ms1
+    res["speedup_vs_per_transform"] = ms3 / ms1
+    print(json.dumps({"config": "ragged", "metric": "ragged batch GB/s on sum(16*N_i)", "unit": "GB/s",
+                      "results": res}), flush=True)
+    return 0
+
+
+def run_serving(args):
+    """Open-loop Poisson arrivals; each request batch ~ U{1..256}, N uniform over
+    {2^k,3*2^k,5*2^k,7*2^k} in [16, 16384]; 4 GiB budget; continuous batching vs the serial queue."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    fam = np.asarray(synth.size_family(16, 16384))
+    rng = np.random.Generator(np.random.Philox(key=synth.DEFAULT_SEED))
+    templates = 128
+    tn = fam[rng.integers(0, fam.size, size=templates)]
+    tb = rng.integers(1, 257, size=templates)
+    t_in, t_out = [], []
+    for i in range(templates):
+        x = synth.uniform_flat(synth.DEFAULT_SEED + i, 0, int(tn[i] * tb[i]))
+        t_in.append(torch.from_numpy(x.view(np.float32)).pin_memory())
+        t_out.append(torch.empty_like(t_in[-1]).pin_memory())
+    budget = 4 << 30
+    rates = [1000, 2000, 5000, 10000, 20000, 50000]
+    results = {}
+
+    def drive(srv, rate, count, seed):
+        r = np.random.Generator(np.random.Philox(key=seed))
+        pick = r.integers(0, templates, size=count)
+        arr = np.cumsum(r.exponential(1.0 / rate, size=count))
+        arr -= arr[0]
+        srv.reset_stats()
+        tickets = srv.replay([int(tn[k]) for k in pick], [int(tb[k]) for k in pick], [-1] * count,
+                             [t_in[k] for k in pick], [t_out[k] for k in pick], arr)
+        for t in tickets:
+            srv.wait(t, 300.0)
+        st = srv.stats()
+        for t in tickets:
+            srv.release(t)
+        return st
+
+    with gbfft.Server(mem_budget_bytes=budget, n_streams=4) as srv:
+        for n in fam.tolist():
+            srv.prepare(int(n), -1)
+        drive(srv, 5000, 1000, 7)  # warm-up
+        for rate in rates:
+            count = 20000 if rate >= 5000 else 10 * rate // 1000 * 1000
+            st = drive(srv, rate, count, rate)
+            results[str(rate)] = dict(st, requests=count, offered_req_per_s=rate)
+    serial = {}
+    with gbfft.Server(mem_budget_bytes=budget, n_streams=1, serial=True) as srv:
+        for n in fam.tolist():
+            srv.prepare(int(n), -1)
+        drive(srv, 1000, 500, 8)
+        for rate in (1000, 5000):
+            st = drive(srv, rate, 3000, rate + 1)
+            serial[str(rate)] = dict(st, requests=3000, offered_req_per_s=rate)
+    print(json.dumps({"config": "serving", "metric": "serving p50/p99 latency (s) and throughput",
+                      "budget_bytes": budget, "streams": 4, "request_templates": templates,
+                      "batching": results, "serial_queue": serial}), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != "sweep":
+        return {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving}[args.config](args)
     return run_gpu(args)
 
 
