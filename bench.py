@@ -551,6 +551,7 @@ def run_ragged(args):
         res["ragged_graph_tuned_us"] = 1e3 * ms1
         res["ragged_gbs"] = nbytes / (ms1 * 1e-3) / 1e9
         res["items"] = rp.num_items()
+        res["queue_order"] = gbfft.gbfft_ragged_queue_order(rp.handle)
         res["tile_splits"] = {str(n): gbfft.gbfft_ragged_tile_split(rp.handle, int(n))
                               for n in sorted(set(sizes.tolist()))}
     # (i) one launch per distinct length over a grouped copy of the data

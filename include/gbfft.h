@@ -202,13 +202,19 @@ gbfft_status gbfft_plan_ragged(gbfft_plan *out, const int64_t *n, const int64_t 
 gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void *cuda_stream);
 
 /*
- * Tile-shape autotuner for a ragged plan: for each length class, heaviest
- * first, tries 1, 2, 4 and 8 items per full tile (rows per item = T/split),
+ * Tile-shape autotuner for a ragged plan: tries both queue orders, then for
+ * each length class, heaviest first, 1, 2, 4 and 8 items per full tile
+ * (rows per item = T/split),
  * timing the whole persistent launch on `in`/`out` (median of `reps` after
  * one warm-up; `out` is overwritten) and keeps the fastest shapes.  *best_ms
  * (may be NULL) receives the best median time.  Synchronous.
  */
 gbfft_status gbfft_ragged_autotune(gbfft_plan p, const void *in, void *out, int reps, float *best_ms);
+
+/* Queue order the plan uses (-1 if not a ragged plan): 1 (default) keeps the
+ * items of one length together, heaviest length first; 0 orders all items by
+ * work, heaviest first.  The autotuner tries both. */
+int gbfft_ragged_queue_order(gbfft_plan p);
 
 /* Number of work items in the plan's queue (-1 if not a ragged plan). */
 int64_t gbfft_ragged_num_items(gbfft_plan p);

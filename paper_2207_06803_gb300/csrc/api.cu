@@ -189,6 +189,7 @@ gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction,
         st = GBFFT_ERR_OOM;
     }
     if (st == GBFFT_OK && prepare_tc(*tv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && (p->grid_cap = tc_grid(*tv)) <= 0) st = GBFFT_ERR_CUDA;
     if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw, n, radix, tv->nstages);
     if (st == GBFFT_OK && launch_tc_fragments(p->tc_frag, p->tc_prec, direction, 0) != cudaSuccess)
         st = GBFFT_ERR_CUDA;
@@ -281,7 +282,8 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
 // Enqueue the transform of `rows` rows from `in` to `out` (device pointers).
 cudaError_t run_device(gbfft_plan p, const float2* in, float2* out, int64_t rows, cudaStream_t s) {
     if (p->kind == kPlanTensorCore)
-        return launch_tc(*p->tcv, p->tc_prec, p->direction, in, out, p->tw, p->tc_frag, (long long)rows, s);
+        return launch_tc(*p->tcv, p->tc_prec, p->direction, in, out, p->tw, p->tc_frag, (long long)rows,
+                         p->grid_cap, s);
     if (p->kind == kPlanSingle)
         return launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)rows, p->grid_cap, s);
     cudaError_t e = launch_cols(*p->cv_m, 1, p->direction, in, p->ws, p->tw_m, p->post, (long long)rows,
@@ -510,6 +512,11 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds) {
         return GBFFT_ERR_INVALID_ARG;
     ragged_set_wait_ns(p->ragged, (long long)nanoseconds);
     return GBFFT_OK;
+}
+
+int gbfft_ragged_queue_order(gbfft_plan p) {
+    if (!p || p->kind != kPlanRagged) return -1;
+    return ragged_queue_order(p->ragged);
 }
 
 int gbfft_ragged_tile_split(gbfft_plan p, int64_t n) {

@@ -1,4 +1,4 @@
-// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16, 32}, fully unrolled.
+// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16, 32, 64}, fully unrolled.
 //
 // Each codelet computes A = DFT_r a in place on r complex values held in
 // registers, natural order in and out, with DFT_r[m][k] = w^(m*k) and
@@ -6,7 +6,7 @@
 // are the "DFT(r)" generators of Table I evaluated as straight-line code, the
 // GPU counterpart of the small solved sub-problems a DFT planner bottoms out in
 // (Sec. III).  Composite codelets use the split of Eq. 2 internally
-// (DFT_8 = 2 x 4, DFT_16 = 4 x 4, DFT_32 = 2 x 16); the odd primes use the symmetric
+// (DFT_8 = 2 x 4, DFT_16 = 4 x 4, DFT_32 = 2 x 16, DFT_64 = 8 x 8); the odd primes use the symmetric
 // sum/difference form of the direct DFT.
 #pragma once
 #include <cuda_runtime.h>
@@ -158,6 +158,79 @@ struct Dft<S, 32> {
             const float2 t = mul_w32<S>(o[k], k);
             a[k] = cadd(e[k], t);
             a[k + 16] = csub(e[k], t);
+        }
+    }
+};
+
+// cos(pi*j/32), j = 0..16.
+__device__ __forceinline__ constexpr float cos_pi32(int j) {
+    return j == 0 ? 1.0f
+         : j == 1 ? 0.99518472667219688624f
+         : j == 2 ? 0.98078528040323044913f
+         : j == 3 ? 0.95694033573220886494f
+         : j == 4 ? 0.92387953251128675613f
+         : j == 5 ? 0.88192126434835502971f
+         : j == 6 ? 0.83146961230254523708f
+         : j == 7 ? 0.77301045336273696081f
+         : j == 8 ? 0.70710678118654752440f
+         : j == 9 ? 0.63439328416364549822f
+         : j == 10 ? 0.55557023301960222474f
+         : j == 11 ? 0.47139673682599764856f
+         : j == 12 ? 0.38268343236508977173f
+         : j == 13 ? 0.29028467725446236764f
+         : j == 14 ? 0.19509032201612826785f
+         : j == 15 ? 0.09801714032956060199f
+                   : 0.0f;
+}
+
+// a * w64^e for 0 <= e < 64, w64 = exp(S*2*pi*i/64) = (cos(pi e/32), S sin(pi e/32)),
+// with the angle reduced to the first octant by quadrant symmetry.
+template <int S>
+__device__ __forceinline__ float2 mul_w64(float2 a, int e) {
+    e &= 63;
+    if (e == 0) return a;
+    if (e == 16) return mul_si<S>(a);
+    if (e == 32) return make_float2(-a.x, -a.y);
+    if (e == 48) return mul_si<-S>(a);
+    float c, s;
+    if (e < 16) {
+        c = cos_pi32(e);
+        s = cos_pi32(16 - e);
+    } else if (e < 32) {
+        c = -cos_pi32(32 - e);
+        s = cos_pi32(e - 16);
+    } else if (e < 48) {
+        c = -cos_pi32(e - 32);
+        s = -cos_pi32(48 - e);
+    } else {
+        c = cos_pi32(64 - e);
+        s = -cos_pi32(e - 48);
+    }
+    return mul_const<S>(a, c, s);
+}
+
+// DFT_64 as 8 x 8 (K = M = 8 in Eq. 2):
+//   X[j1 + 8*j2] = sum_k w8^(j2*k) * w64^(j1*k) * sum_m w8^(j1*m) x[8m + k].
+template <int S>
+struct Dft<S, 64> {
+    __device__ __forceinline__ static void run(float2* a) {
+        float2 z[8][8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+#pragma unroll
+            for (int m = 0; m < 8; ++m) z[k][m] = a[8 * m + k];
+            Dft<S, 8>::run(z[k]);
+#pragma unroll
+            for (int j1 = 1; j1 < 8; ++j1) z[k][j1] = mul_w64<S>(z[k][j1], j1 * k);
+        }
+#pragma unroll
+        for (int j1 = 0; j1 < 8; ++j1) {
+            float2 c[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c[k] = z[k][j1];
+            Dft<S, 8>::run(c);
+#pragma unroll
+            for (int j2 = 0; j2 < 8; ++j2) a[j1 + 8 * j2] = c[j2];
         }
     }
 };

@@ -69,8 +69,10 @@ const TcVariant* tc_variant_for(int64_t n);
 cudaError_t prepare_tc(const TcVariant& v);
 // frag: 32 lanes x 32 words; prec as above; sign = exponent sign of the transform.
 cudaError_t launch_tc_fragments(uint32_t* frag, int prec, int sign, cudaStream_t s);
+// Resident CTAs of the (persistent) tensor-core kernel on the current device.
+int tc_grid(const TcVariant& v);
 cudaError_t launch_tc(const TcVariant& v, int prec, int direction, const float2* in, float2* out, const float2* tw,
-                      const uint32_t* frag, long long batch, cudaStream_t s);
+                      const uint32_t* frag, long long batch, int grid_cap, cudaStream_t s);
 
 // Ragged-batch plans (ragged.cu).
 struct RaggedState;
@@ -87,6 +89,7 @@ void ragged_set_wait_ns(RaggedState* r, long long ns);
 gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void* out, int* status, int reps,
                              float* best_ms);
 int ragged_class_split(const RaggedState* r, int64_t n);
+int ragged_queue_order(const RaggedState* r);
 bool ragged_supported(int64_t n);
 
 // Per-translation-unit variant tables, gathered by the registry in api.cu.

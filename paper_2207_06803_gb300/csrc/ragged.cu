@@ -120,6 +120,7 @@ struct RaggedState {
     std::vector<int64_t> n, off;
     std::vector<std::vector<int64_t>> members;  // transform indices per class
     int split[kRaggedClasses];                  // tile shape: rows per item = T_c / split[c]
+    int order = 1;                              // queue order: 0 = heaviest item first, 1 = grouped by class
     std::vector<RaggedItem> items;
     std::vector<long long> row_offs;
     RaggedItem* d_items = nullptr;
@@ -157,7 +158,12 @@ void ragged_destroy(RaggedState* r) {
 }
 
 // Items from the current tile shapes: class groups cut into items of
-// ceil(T_c / split_c) rows, then ordered by work (rows * N log N) descending.
+// ceil(T_c / split_c) rows.  Order 0: all items by work (rows * N log N),
+// heaviest first (longest-processing-time list scheduling).  Order 1: items
+// stay grouped by class, classes ordered by item work, heaviest first, so
+// that CTAs claiming neighbouring items run the same class's code (the
+// kernel holds one fully unrolled schedule per class; interleaving classes
+// thrashes the instruction cache).
 static gbfft_status ragged_build_items(RaggedState* r) {
     r->items.clear();
     r->row_offs.clear();
@@ -181,7 +187,16 @@ static gbfft_status ragged_build_items(RaggedState* r) {
             pend.push_back(std::move(p));
         }
     }
-    std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
+    if (r->order == 0) {
+        std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
+    } else {
+        std::vector<double> cls_cost(kRaggedClasses, 0.0);
+        for (const Pending& p : pend) cls_cost[p.cls] = std::max(cls_cost[p.cls], p.cost);
+        std::stable_sort(pend.begin(), pend.end(), [&](const Pending& a, const Pending& b) {
+            if (a.cls != b.cls) return cls_cost[a.cls] > cls_cost[b.cls] || (cls_cost[a.cls] == cls_cost[b.cls] && a.cls > b.cls);
+            return a.cost > b.cost;
+        });
+    }
     for (const Pending& p : pend) {
         RaggedItem it;
         it.cls = p.cls;
@@ -415,6 +430,14 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
     if (reps < 1) reps = 1;
     float best = 0.f;
     gbfft_status st = measure(&best);
+    {
+        const int keep = r->order;
+        r->order = 1 - keep;
+        float ms = 0.f;
+        if (st == GBFFT_OK) st = measure(&ms);
+        if (st == GBFFT_OK && ms < best) best = ms;
+        else r->order = keep;
+    }
     std::vector<int> order;
     for (int c = 0; c < kRaggedClasses; ++c)
         if (!r->members[c].empty()) order.push_back(c);
@@ -447,6 +470,8 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
     if (best_ms) *best_ms = best;
     return st;
 }
+
+int ragged_queue_order(const RaggedState* r) { return r->order; }
 
 int ragged_class_split(const RaggedState* r, int64_t n) {
     const int c = class_of(n);

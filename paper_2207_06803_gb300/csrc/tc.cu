@@ -55,23 +55,45 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
     }
 }
 
-// Split two floats into packed (hi, lo) half-type pairs; element 0 in the low half.
+// Split two floats into packed (hi, lo) half-type pairs; element 0 in the low
+// half.  hi = RN(x) with one packed conversion, lo = RN(x - hi) where x - hi
+// is exact in FP32.
 template <int PREC>
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
     if constexpr (PREC == kTcFp16) {
-        const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
-        const __half l0 = __float2half_rn(x0 - __half2float(h0)), l1 = __float2half_rn(x1 - __half2float(h1));
-        const __half2 H = __halves2half2(h0, h1), L = __halves2half2(l0, l1);
+        const __half2 H = __floats2half2_rn(x0, x1);
+        const float2 h = __half22float2(H);
+        const __half2 L = __floats2half2_rn(x0 - h.x, x1 - h.y);
         hi = *reinterpret_cast<const uint32_t*>(&H);
         lo = *reinterpret_cast<const uint32_t*>(&L);
     } else {
-        const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-        const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-        const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-        const __nv_bfloat162 H = __halves2bfloat162(h0, h1), L = __halves2bfloat162(l0, l1);
+        const __nv_bfloat162 H = __floats2bfloat162_rn(x0, x1);
+        const float2 h = __bfloat1622float2(H);
+        const __nv_bfloat162 L = __floats2bfloat162_rn(x0 - h.x, x1 - h.y);
         hi = *reinterpret_cast<const uint32_t*>(&H);
         lo = *reinterpret_cast<const uint32_t*>(&L);
     }
+}
+
+// Shared-memory layout of exchange X (after stage X): an XOR swizzle of the
+// tile element index that only rewrites bits 0-3 (the 8-byte bank slot) from
+// bits >= 4, so it is a bijection on the tile.  It makes the mma-fragment
+// reads of the next stage (lanes differ in element bits 0-1 and in the bits of
+// q*N/16) and the accumulator writes of this stage (lanes differ in the bits
+// of m*L and of the column) land on 16 distinct slots per half-warp.
+template <int X>
+__device__ __forceinline__ int tc_swz(int i) {
+    if constexpr (X == 0) {
+        return i ^ (((i >> 5) & 3) << 2) ^ (((i >> 9) & 3) << 2);
+    } else {
+        return i ^ ((i >> 4) & 1) ^ (((i >> 5) & 1) << 3) ^ (((i >> 9) & 3) << 2);
+    }
+}
+
+// Exchange index of the stage with this L: 1 -> 0, 16 -> 1, 256 -> 2.
+template <int L>
+constexpr int tc_stage_index() {
+    return L == 1 ? 0 : (L == 16 ? 1 : 2);
 }
 
 // A-fragments of M for this lane: frag[(mt*2 + kt)*4 + r] (hi) and +16 (lo).
@@ -107,7 +129,7 @@ __device__ __forceinline__ void tc_stage(const ContigIO<N>& io, float2* sm, cons
             if constexpr (FIRST) {
                 x[i] = (t < nvalid) ? io.ld(t, n) : make_float2(0.f, 0.f);
             } else {
-                x[i] = sm[spad<PS>(t * N + n)];
+                x[i] = sm[tc_swz<tc_stage_index<L>() - 1>(t * N + n)];
             }
             if constexpr (L > 1) {
                 if (q > 0) x[i] = twiddle<S>(x[i], __ldg(&tw[(q - 1) * L + k]));
@@ -169,17 +191,33 @@ __device__ __forceinline__ void tc_stage(const ContigIO<N>& io, float2* sm, cons
 #pragma unroll
     for (int it = 0; it < PER; ++it) {
         const int tile = warp + it * WARPS;
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const int B = tile * 8 + 2 * c + (o & 1);
-            const int m = (o < 2) ? g : g + 8;
+        if constexpr (LAST && NR % 2 == 0) {
+            // NR even: columns 2c, 2c+1 are adjacent elements j, j+1 (j even) of
+            // one output row, so each m is one aligned 16-byte store.
+            const int B = tile * 8 + 2 * c;
             const int t = B / NR, j = B % NR;
-            const int b = j / L, k = j % L;
-            const int n = b * L * R + m * L + k;
-            if constexpr (LAST) {
-                if (t < nvalid) io.st(t, n, outv[it][o]);
-            } else {
-                sm[spad<PS>(t * N + n)] = outv[it][o];
+            if (t < nvalid) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int m = g + 8 * h;
+                    float4* dst = reinterpret_cast<float4*>(io.out + t * N + m * L + j);
+                    *dst = make_float4(outv[it][2 * h].x, outv[it][2 * h].y, outv[it][2 * h + 1].x,
+                                       outv[it][2 * h + 1].y);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int B = tile * 8 + 2 * c + (o & 1);
+                const int m = (o < 2) ? g : g + 8;
+                const int t = B / NR, j = B % NR;
+                const int b = j / L, k = j % L;
+                const int n = b * L * R + m * L + k;
+                if constexpr (LAST) {
+                    if (t < nvalid) io.st(t, n, outv[it][o]);
+                } else {
+                    sm[tc_swz<tc_stage_index<L>()>(t * N + n)] = outv[it][o];
+                }
             }
         }
     }
@@ -197,12 +235,12 @@ __device__ __forceinline__ void tc_stages(const ContigIO<N>& io, float2* sm, con
 }
 
 // frag: per lane, 16 hi words then 16 lo words (see k_tc_fragments).
+// Persistent: each CTA keeps the DFT_16 fragments in registers and walks the
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 template <int N, int S, int PREC, int T, int TPB, int PS>
 __global__ void __launch_bounds__(TPB) k_stockham_tc(const float2* in, float2* out, const float2* __restrict__ tw,
                                                      const uint32_t* __restrict__ frag, long long batch) {
     extern __shared__ float2 sm[];
-    const long long tile = blockIdx.x;
-    const int nvalid = tile_rows(tile, T, batch);
     const int lane = threadIdx.x & 31;
     TcFrags F;
 #pragma unroll
@@ -210,8 +248,13 @@ __global__ void __launch_bounds__(TPB) k_stockham_tc(const float2* in, float2* o
         F.h[r] = __ldg(&frag[lane * 32 + r]);
         F.l[r] = __ldg(&frag[lane * 32 + 16 + r]);
     }
-    const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
-    tc_stages<N, S, PREC, T, TPB, PS, 1>(io, sm, tw, F, nvalid);
+    const long long ntiles = (batch + T - 1) / T;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tile != blockIdx.x) __syncthreads();  // the previous tile's last shared-memory reads are done
+        const int nvalid = tile_rows(tile, T, batch);
+        const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
+        tc_stages<N, S, PREC, T, TPB, PS, 1>(io, sm, tw, F, nvalid);
+    }
 }
 
 // A-fragment table of M = [[Fr, -Fi], [Fi, Fr]] (DFT_16 over the reals) for
@@ -271,7 +314,7 @@ inline TcVariant make_tc_variant() {
     v.rows = T;
     v.tpb = TPB;
     v.nstages = nst;
-    v.smem = nst > 1 ? (int)(smem_elems<T, N, PS>() * sizeof(float2)) : 0;
+    v.smem = nst > 1 ? (int)(T * N * sizeof(float2)) : 0;
     v.k[0][0] = (const void*)&k_stockham_tc<N, -1, kTcFp16, T, TPB, PS>;
     v.k[0][1] = (const void*)&k_stockham_tc<N, +1, kTcFp16, T, TPB, PS>;
     v.k[1][0] = (const void*)&k_stockham_tc<N, -1, kTcBf16, T, TPB, PS>;
@@ -291,10 +334,20 @@ const TcVariant* tc_variant_for(int64_t n) {
     return nullptr;
 }
 
+int tc_grid(const TcVariant& v) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.k[0][0], v.tpb, (size_t)v.smem) != cudaSuccess)
+        return 0;
+    return per_sm * sms;
+}
+
 cudaError_t launch_tc(const TcVariant& v, int prec, int direction, const float2* in, float2* out, const float2* tw,
-                      const uint32_t* frag, long long batch, cudaStream_t s) {
+                      const uint32_t* frag, long long batch, int grid_cap, cudaStream_t s) {
     if (batch <= 0) return cudaSuccess;
-    const long long blocks = (batch + v.rows - 1) / v.rows;
+    long long blocks = (batch + v.rows - 1) / v.rows;
+    if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
     void* args[] = {(void*)&in, (void*)&out, (void*)&tw, (void*)&frag, (void*)&batch};
     const void* fn = v.k[prec][direction == GBFFT_FORWARD ? 0 : 1];
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.tpb), args, (size_t)v.smem, s);

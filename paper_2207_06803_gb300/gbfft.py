@@ -69,6 +69,7 @@ PROTOTYPES = {
     "gbfft_ragged_autotune": (_c_int, [_c_vp, _c_vp, _c_vp, _c_int, ctypes.POINTER(ctypes.c_float)]),
     "gbfft_ragged_num_items": (_c_i64, [_c_vp]),
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
+    "gbfft_ragged_queue_order": (_c_int, [_c_vp]),
     "gbfft_ragged_set_item_ready": (_c_int, [_c_vp, _c_i64, _c_int]),
     "gbfft_ragged_set_wait_limit": (_c_int, [_c_vp, _c_i64]),
     "gbfft_server_create": (_c_int, [ctypes.POINTER(_c_vp), _c_size, _c_int, _c_int]),
@@ -253,6 +254,10 @@ def gbfft_ragged_num_items(plan: int) -> int:
 
 def gbfft_ragged_tile_split(plan: int, n: int) -> int:
     return int(lib().gbfft_ragged_tile_split(plan, n))
+
+
+def gbfft_ragged_queue_order(plan: int) -> int:
+    return int(lib().gbfft_ragged_queue_order(plan))
 
 
 def gbfft_ragged_set_item_ready(plan: int, item: int, ready: int) -> None:
