@@ -19,19 +19,20 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-template <int S, int N, int E, int PS, int... Rs>
+template <int S, int N, int T, int PS, int... Rs>
 __device__ __noinline__ void ragged_item(const float2* in, float2* out, const long long* s_off, float2* sm,
                                             const float2* __restrict__ tw, int nvalid) {
-    constexpr int T = kRaggedThreads * E / N;
-    static_assert(T >= 1 && T * N / E == kRaggedThreads, "every class runs 256 threads");
+    constexpr int TPB = kRaggedThreads;
+    constexpr int E = capacity_of_r<N, T, TPB, Rs...>();
+    static_assert(T >= 1 && T <= kRaggedThreads && E <= 32, "class tile shape");
     const IndexedIO<N> io{in, out, s_off};
     float2 v[E];
-    gather_global<N, E, T, First<Rs...>::value>(v, io, nvalid);
-    run_stages<N, S, E, T, PS, true, 0, 1, Rs...>(v, io, sm, tw, nvalid);
+    gather_global<N, E, T, First<Rs...>::value, IndexedIO<N>, TPB>(v, io, nvalid);
+    run_stages_t<N, S, E, T, PS, TPB, true, 0, 1, Rs...>(v, io, sm, tw, nvalid);
 }
 
 template <int S>
-__global__ void __launch_bounds__(kRaggedThreads) k_ragged(const float2* in, float2* out, const RaggedItem* items,
+__global__ void __launch_bounds__(kRaggedThreads, 3) k_ragged(const float2* in, float2* out, const RaggedItem* items,
                                                            int nitems, const long long* offs,
                                                            const float2* __restrict__ tw,
                                                            const int* __restrict__ tw_off, int* counter, int* status,
@@ -70,9 +71,9 @@ __global__ void __launch_bounds__(kRaggedThreads) k_ragged(const float2* in, flo
         __syncthreads();
         const float2* twc = tw + tw_off[d.cls];
         switch (d.cls) {
-#define GBFFT_RAGGED_CASE(idx, N, E, PS, ...)                                      \
+#define GBFFT_RAGGED_CASE(idx, N, T, PS, ...)                                      \
     case idx:                                                                     \
-        ragged_item<S, N, E, PS, __VA_ARGS__>(in, out, s_off, sm, twc, d.count); \
+        ragged_item<S, N, T, PS, __VA_ARGS__>(in, out, s_off, sm, twc, d.count); \
         break;
             GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_CASE)
 #undef GBFFT_RAGGED_CASE
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(kRaggedThreads) k_ragged(const float2* in, flo
 namespace {
 
 struct ClassInfo {
-    int n, e, t, ps, nstages;
+    int n, t, ps, nstages;
     int radix[kMaxStages];
 };
 
@@ -95,8 +96,7 @@ constexpr int count_of() {
     return (int)sizeof...(Rs);
 }
 
-#define GBFFT_RAGGED_INFO(idx, N, E, PS, ...) \
-    ClassInfo{N, E, kRaggedThreads * E / N, PS, count_of<__VA_ARGS__>(), {__VA_ARGS__}},
+#define GBFFT_RAGGED_INFO(idx, N, T, PS, ...) ClassInfo{N, T, PS, count_of<__VA_ARGS__>(), {__VA_ARGS__}},
 const ClassInfo kClasses[kRaggedClasses] = {GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_INFO)};
 #undef GBFFT_RAGGED_INFO
 

@@ -1,6 +1,9 @@
 // Single-pass variants for lengths p * 2^k (p = 3, 5, 7) up to 4096: one
-// radix-p stage first, then power-of-two stages.  E is a multiple of every
-// radix in the schedule.
+// radix-p stage first, then power-of-two stages.  The first entry of each
+// length (GBFFT_ROWS_T: explicit thread count, sized by the radix-16 stages;
+// the radix-p stage runs ceil(butterflies/threads) per thread) is the
+// default; the GBFFT_ROWS entries (E a multiple of every radix) remain as
+// alternatives.  Pad shifts come from a shared-memory bank model.
 #include "variants.cuh"
 
 namespace gbfft {
@@ -8,34 +11,66 @@ namespace gbfft {
 static const RowsVariant kMixed[] = {
     GBFFT_ROWS(3, 3, 128, 0, 3),
     GBFFT_ROWS(6, 6, 128, 4, 3, 2),
+    GBFFT_ROWS_T(6, 768, 256, 0, 3, 2),
     GBFFT_ROWS(12, 12, 64, 4, 3, 4),
+    GBFFT_ROWS_T(12, 768, 256, 0, 3, 4),
+    GBFFT_ROWS_T(24, 384, 128, 0, 3, 8),
     GBFFT_ROWS(24, 24, 64, 4, 3, 8),
     GBFFT_ROWS(48, 12, 16, 4, 3, 4, 4),
+    GBFFT_ROWS_T(48, 192, 64, 4, 3, 16),
     GBFFT_ROWS(96, 24, 16, 4, 3, 8, 4),
+    GBFFT_ROWS_T(96, 192, 32, 4, 3, 2, 16),
+    GBFFT_ROWS_T(192, 192, 16, 0, 3, 4, 16),
     GBFFT_ROWS(192, 24, 8, 4, 3, 8, 8),
+    GBFFT_ROWS_T(384, 192, 8, 0, 3, 8, 16),
     GBFFT_ROWS(384, 24, 4, 4, 3, 8, 4, 4),
+    GBFFT_ROWS_T(768, 192, 4, 4, 3, 16, 16),
     GBFFT_ROWS(768, 24, 2, 4, 3, 8, 8, 4),
+    GBFFT_ROWS_T(1536, 192, 2, 4, 3, 16, 16, 2),
+    GBFFT_ROWS_T(1536, 192, 4, 4, 3, 16, 32),
     GBFFT_ROWS(1536, 24, 2, 4, 3, 8, 8, 8),
-    GBFFT_ROWS(3072, 24, 1, 4, 3, 8, 8, 8, 2),
+    GBFFT_ROWS_T(3072, 192, 1, 4, 3, 16, 16, 4),
+    GBFFT_ROWS_T(3072, 192, 2, 4, 3, 16, 32, 2),
+    GBFFT_ROWS_T(3072, 192, 2, 4, 3, 32, 32),
     GBFFT_ROWS(5, 5, 128, 0, 5),
     GBFFT_ROWS(10, 10, 128, 4, 5, 2),
+    GBFFT_ROWS_T(10, 640, 128, 0, 5, 2),
+    GBFFT_ROWS_T(20, 640, 128, 0, 5, 4),
     GBFFT_ROWS(20, 20, 64, 4, 5, 4),
+    GBFFT_ROWS_T(40, 320, 64, 0, 5, 8),
     GBFFT_ROWS(40, 40, 64, 4, 5, 8),
+    GBFFT_ROWS_T(80, 160, 32, 5, 5, 16),
     GBFFT_ROWS(80, 20, 16, 4, 5, 4, 4),
+    GBFFT_ROWS_T(160, 160, 16, 0, 5, 2, 16),
     GBFFT_ROWS(160, 40, 16, 4, 5, 8, 4),
+    GBFFT_ROWS_T(320, 160, 8, 0, 5, 4, 16),
     GBFFT_ROWS(320, 40, 8, 4, 5, 8, 8),
+    GBFFT_ROWS_T(640, 160, 4, 0, 5, 8, 16),
     GBFFT_ROWS(640, 40, 4, 4, 5, 8, 4, 4),
+    GBFFT_ROWS_T(1280, 160, 2, 5, 5, 16, 16),
     GBFFT_ROWS(1280, 40, 2, 4, 5, 8, 8, 4),
+    GBFFT_ROWS_T(2560, 160, 1, 5, 5, 16, 16, 2),
+    GBFFT_ROWS_T(2560, 160, 2, 4, 5, 16, 32),
     GBFFT_ROWS(2560, 40, 2, 4, 5, 8, 8, 8),
     GBFFT_ROWS(7, 7, 128, 0, 7),
     GBFFT_ROWS(14, 14, 128, 4, 7, 2),
+    GBFFT_ROWS_T(14, 896, 128, 0, 7, 2),
     GBFFT_ROWS(28, 28, 64, 4, 7, 4),
+    GBFFT_ROWS_T(28, 896, 128, 0, 7, 4),
     GBFFT_ROWS(56, 56, 32, 4, 7, 8),
+    GBFFT_ROWS_T(56, 448, 64, 0, 7, 8),
+    GBFFT_ROWS_T(112, 224, 32, 4, 7, 16),
     GBFFT_ROWS(112, 28, 16, 4, 7, 4, 4),
+    GBFFT_ROWS_T(224, 224, 16, 0, 7, 2, 16),
     GBFFT_ROWS(224, 56, 16, 4, 7, 8, 4),
+    GBFFT_ROWS_T(448, 224, 8, 0, 7, 4, 16),
     GBFFT_ROWS(448, 56, 8, 4, 7, 8, 8),
+    GBFFT_ROWS_T(896, 224, 4, 0, 7, 8, 16),
     GBFFT_ROWS(896, 56, 4, 4, 7, 8, 4, 4),
+    GBFFT_ROWS_T(1792, 224, 2, 4, 7, 16, 16),
     GBFFT_ROWS(1792, 56, 2, 4, 7, 8, 8, 4),
+    GBFFT_ROWS_T(3584, 224, 1, 4, 7, 16, 16, 2),
+    GBFFT_ROWS_T(3584, 224, 2, 4, 7, 16, 32),
     GBFFT_ROWS(3584, 56, 2, 4, 7, 8, 8, 8),
 };
 

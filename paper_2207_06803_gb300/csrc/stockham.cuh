@@ -86,14 +86,23 @@ struct IndexedIO {
     __device__ __forceinline__ void st(int t, int n, float2 v) const { out[off[t] + n] = v; }
 };
 
+// Butterflies of radix R per thread when TPB threads share the T*N/R
+// butterflies of a stage (the last round may leave threads idle).
+template <int N, int T, int TPB, int R>
+constexpr int stage_nb() {
+    return (T * N / R + TPB - 1) / TPB;
+}
+
 // Stage-1 operands of this thread's butterflies, straight from HBM.
-template <int N, int E, int T, int R, class IO>
+template <int N, int E, int T, int R, class IO, int TPB = T * N / E>
 __device__ __forceinline__ void gather_global(float2 (&v)[E], const IO& io, int nvalid) {
-    constexpr int TPB = T * N / E, NB = E / R, NR = N / R;
+    constexpr int NB = stage_nb<N, T, TPB, R>(), NR = N / R, NBT = T * N / R;
+    static_assert(NB * R <= E, "register capacity too small for this stage");
     const int tid = threadIdx.x;
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
         const int B = tid + u * TPB;
+        if (NBT % TPB != 0 && B >= NBT) break;
         const int t = B / NR, j = B % NR;
 #pragma unroll
         for (int q = 0; q < R; ++q) v[u * R + q] = (t < nvalid) ? io.ld(t, j + q * NR) : make_float2(0.f, 0.f);
@@ -101,13 +110,15 @@ __device__ __forceinline__ void gather_global(float2 (&v)[E], const IO& io, int 
 }
 
 // Stage operands from the shared-memory tile.
-template <int N, int E, int T, int PS, int R>
+template <int N, int E, int T, int PS, int R, int TPB = T * N / E>
 __device__ __forceinline__ void gather_smem(float2 (&v)[E], const float2* sm) {
-    constexpr int TPB = T * N / E, NB = E / R, NR = N / R;
+    constexpr int NB = stage_nb<N, T, TPB, R>(), NR = N / R, NBT = T * N / R;
+    static_assert(NB * R <= E, "register capacity too small for this stage");
     const int tid = threadIdx.x;
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
         const int B = tid + u * TPB;
+        if (NBT % TPB != 0 && B >= NBT) break;
         const int t = B / NR, j = B % NR;
 #pragma unroll
         for (int q = 0; q < R; ++q) v[u * R + q] = sm[spad<PS>(t * N + j + q * NR)];
@@ -117,18 +128,23 @@ __device__ __forceinline__ void gather_smem(float2 (&v)[E], const float2* sm) {
 // Stages from the one whose operands `v` already holds to the end.  SYNC0:
 // synchronise before the first shared-memory write (needed when earlier
 // readers of the tile buffer may still be running).
-template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest, class IO>
-__device__ __forceinline__ void run_stages(float2 (&v)[E], const IO& io, float2* sm, const float2* __restrict__ tw,
-                                           int nvalid) {
-    constexpr int TPB = T * N / E;
-    constexpr int NB = E / R;  // butterflies per thread in this stage
-    constexpr int NR = N / R;  // butterflies per row
+// The stage loop with an explicit thread count TPB: stage s runs
+// ceil(T*N/R_s / TPB) butterflies per thread (guarded when uneven), so a
+// schedule may mix radices whose butterfly counts do not divide the threads.
+template <int N, int S, int E, int T, int PS, int TPB, bool SYNC0, int TWO, int L, int R, int... Rest, class IO>
+__device__ __forceinline__ void run_stages_t(float2 (&v)[E], const IO& io, float2* sm,
+                                             const float2* __restrict__ tw, int nvalid) {
+    constexpr int NB = stage_nb<N, T, TPB, R>();  // butterflies per thread in this stage
+    constexpr int NR = N / R;                     // butterflies per row
+    constexpr int NBT = T * N / R;                // butterflies in the tile
+    constexpr bool EVEN = NBT % TPB == 0;
     constexpr bool LAST = sizeof...(Rest) == 0;
-    static_assert(E % R == 0, "radix must divide the elements held per thread");
+    static_assert(NB * R <= E, "register capacity too small for this stage");
     const int tid = threadIdx.x;
 
 #pragma unroll
     for (int u = 0; u < NB; ++u) {
+        if (!EVEN && tid + u * TPB >= NBT) break;
         if constexpr (L > 1) {
             const int B = tid + u * TPB;
             const int k = (B % NR) % L;
@@ -142,6 +158,7 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], const IO& io, float2*
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int B = tid + u * TPB;
+            if (!EVEN && B >= NBT) break;
             const int t = B / NR, j = B % NR;
             if (t < nvalid) {
 #pragma unroll
@@ -153,15 +170,24 @@ __device__ __forceinline__ void run_stages(float2 (&v)[E], const IO& io, float2*
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int B = tid + u * TPB;
+            if (!EVEN && B >= NBT) break;
             const int t = B / NR, j = B % NR;
             const int b = j / L, k = j % L;
 #pragma unroll
             for (int q = 0; q < R; ++q) sm[spad<PS>(t * N + b * L * R + q * L + k)] = v[u * R + q];
         }
         __syncthreads();
-        gather_smem<N, E, T, PS, First<Rest...>::value>(v, sm);
-        run_stages<N, S, E, T, PS, true, TWO + (L > 1 ? (R - 1) * L : 0), L * R, Rest...>(v, io, sm, tw, nvalid);
+        gather_smem<N, E, T, PS, First<Rest...>::value, TPB>(v, sm);
+        run_stages_t<N, S, E, T, PS, TPB, true, TWO + (L > 1 ? (R - 1) * L : 0), L * R, Rest...>(v, io, sm, tw,
+                                                                                                 nvalid);
     }
+}
+
+// Stages with TPB = T*N/E threads (every stage's butterflies divide evenly).
+template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest, class IO>
+__device__ __forceinline__ void run_stages(float2 (&v)[E], const IO& io, float2* sm, const float2* __restrict__ tw,
+                                           int nvalid) {
+    run_stages_t<N, S, E, T, PS, T * N / E, SYNC0, TWO, L, R, Rest...>(v, io, sm, tw, nvalid);
 }
 
 __device__ __forceinline__ int tile_rows(long long tile, int T, long long batch) {
@@ -181,6 +207,33 @@ __global__ void __launch_bounds__(T * N / E) k_stockham_rows(const float2* in, f
     const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
     gather_global<N, E, T, First<Rs...>::value>(v, io, nvalid);
     run_stages<N, S, E, T, PS, false, 0, 1, Rs...>(v, io, sm, tw, nvalid);
+}
+
+// Register capacity for a schedule run by TPB threads: the largest
+// butterflies-per-thread times radix over its stages.
+template <int N, int T, int TPB, int R, int... Rest>
+constexpr int capacity_of_r() {
+    constexpr int here = stage_nb<N, T, TPB, R>() * R;
+    if constexpr (sizeof...(Rest) == 0) {
+        return here;
+    } else {
+        constexpr int rest = capacity_of_r<N, T, TPB, Rest...>();
+        return here > rest ? here : rest;
+    }
+}
+
+// Contiguous rows with an explicit thread count (mixed-radix schedules).
+template <int N, int S, int TPB, int T, int PS, int... Rs>
+__global__ void __launch_bounds__(TPB) k_stockham_rows_t(const float2* in, float2* out,
+                                                          const float2* __restrict__ tw, long long batch) {
+    constexpr int E = capacity_of_r<N, T, TPB, Rs...>();
+    extern __shared__ float2 sm[];
+    const long long tile = blockIdx.x;
+    const int nvalid = tile_rows(tile, T, batch);
+    float2 v[E];
+    const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
+    gather_global<N, E, T, First<Rs...>::value, ContigIO<N>, TPB>(v, io, nvalid);
+    run_stages_t<N, S, E, T, PS, TPB, false, 0, 1, Rs...>(v, io, sm, tw, nvalid);
 }
 
 // Persistent form with register prefetch of the next tile's stage-1 operands.

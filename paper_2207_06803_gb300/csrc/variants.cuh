@@ -39,6 +39,22 @@ inline RowsVariant make_rows_pf_variant() {
                        (const void*)&k_stockham_rows_pf<N, +1, E, T, PS, Rs...>};
 }
 
+template <int N, int TPB, int T, int PS, int... Rs>
+inline RowsVariant make_rows_t_variant() {
+    static_assert(((Rs * ...) == N), "radix schedule must multiply to N");
+    return RowsVariant{kRowsDirect,
+                       N,
+                       capacity_of_r<N, T, TPB, Rs...>(),
+                       T,
+                       TPB,
+                       PS,
+                       (int)sizeof...(Rs),
+                       {Rs...},
+                       (int)(sizeof...(Rs) > 1 ? smem_elems<T, N, PS>() * sizeof(float2) : 0),
+                       (const void*)&k_stockham_rows_t<N, -1, TPB, T, PS, Rs...>,
+                       (const void*)&k_stockham_rows_t<N, +1, TPB, T, PS, Rs...>};
+}
+
 template <int N, int T>
 inline RowsVariant make_small_variant() {
     return RowsVariant{kRowsSmall,
@@ -59,3 +75,4 @@ inline RowsVariant make_small_variant() {
 #define GBFFT_ROWS(N, E, T, PS, ...) ::gbfft::make_rows_variant<N, E, T, PS, __VA_ARGS__>()
 #define GBFFT_ROWS_PF(N, E, T, PS, ...) ::gbfft::make_rows_pf_variant<N, E, T, PS, __VA_ARGS__>()
 #define GBFFT_SMALL(N, T) ::gbfft::make_small_variant<N, T>()
+#define GBFFT_ROWS_T(N, TPB, T, PS, ...) ::gbfft::make_rows_t_variant<N, TPB, T, PS, __VA_ARGS__>()
