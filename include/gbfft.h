@@ -171,6 +171,14 @@ gbfft_status gbfft_variant_info(int64_t n, int index, int *nstages, int *radices
                                 int *threads_per_cta, int *smem_bytes);
 
 /*
+ * Kernel shape of variant `index` for length n: 0 one tile per CTA, 1
+ * persistent with register prefetch, 2 one row per thread staged through
+ * shared memory, 3 persistent with the next tile prefetched by TMA bulk copy
+ * into shared memory (bounded mbarrier waits).  -1 for an index out of range.
+ */
+int gbfft_variant_kind(int64_t n, int index);
+
+/*
  * Read (and clear) the plan's device status word after the stream that ran it
  * has been synchronised.  GBFFT_OK when no kernel reported a problem, else
  * DEVICE_STATUS / TIMEOUT.

@@ -44,11 +44,11 @@ cudaError_t prepare_rows(const RowsVariant& v) {
 }
 
 cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, float2* out, const float2* tw,
-                        long long batch, int grid_cap, cudaStream_t stream) {
+                        long long batch, int grid_cap, cudaStream_t stream, int* status) {
     if (batch <= 0) return cudaSuccess;
     long long blocks = (batch + v.rows - 1) / v.rows;
-    if (v.kind == kRowsPersistent && grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
-    void* args[] = {(void*)&in, (void*)&out, (void*)&tw, (void*)&batch};
+    if ((v.kind == kRowsPersistent || v.kind == kRowsTma) && grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
+    void* args[] = {(void*)&in, (void*)&out, (void*)&tw, (void*)&batch, (void*)&status};
     const void* fn = direction == GBFFT_FORWARD ? v.kfwd : v.kinv;
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.tpb), args, (size_t)v.smem, stream);
 }
@@ -263,7 +263,7 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
         p->variant = variant;
         p->rv = cands[variant];
         if (prepare_rows(*p->rv) != cudaSuccess) st = GBFFT_ERR_CUDA;
-        if (st == GBFFT_OK && p->rv->kind == kRowsPersistent) {
+        if (st == GBFFT_OK && (p->rv->kind == kRowsPersistent || p->rv->kind == kRowsTma)) {
             p->grid_cap = persistent_grid(*p->rv);
             if (p->grid_cap <= 0) st = GBFFT_ERR_CUDA;
         }
@@ -285,7 +285,7 @@ cudaError_t run_device(gbfft_plan p, const float2* in, float2* out, int64_t rows
         return launch_tc(*p->tcv, p->tc_prec, p->direction, in, out, p->tw, p->tc_frag, (long long)rows,
                          p->grid_cap, s);
     if (p->kind == kPlanSingle)
-        return launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)rows, p->grid_cap, s);
+        return launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)rows, p->grid_cap, s, p->status);
     cudaError_t e = launch_cols(*p->cv_m, 1, p->direction, in, p->ws, p->tw_m, p->post, (long long)rows,
                                 (int)p->k_outer, s);
     if (e != cudaSuccess) return e;
@@ -539,6 +539,13 @@ gbfft_status gbfft_variant_info(int64_t n, int index, int* nstages, int* radices
     if (threads_per_cta) *threads_per_cta = v->tpb;
     if (smem_bytes) *smem_bytes = v->smem;
     return GBFFT_OK;
+}
+
+int gbfft_variant_kind(int64_t n, int index) {
+    const RowsVariant* cands[kMaxVariantsPerSize];
+    const int nc = rows_variants_for(n, cands, kMaxVariantsPerSize);
+    if (index < 0 || index >= nc) return -1;
+    return cands[index]->kind;
 }
 
 gbfft_status gbfft_plan_device_status(gbfft_plan p) {

@@ -15,7 +15,8 @@ constexpr int kMaxStages = 8;
 enum RowsKind : int {
     kRowsDirect = 0,      // k_stockham_rows: one tile per CTA
     kRowsPersistent = 1,  // k_stockham_rows_pf: resident CTAs walk tiles with register prefetch
-    kRowsSmall = 2        // k_stockham_small: one row per thread, tile staged through shared memory
+    kRowsSmall = 2,       // k_stockham_small: one row per thread, tile staged through shared memory
+    kRowsTma = 3          // k_stockham_rows_tma: persistent, next tile prefetched by TMA bulk copy
 };
 
 // One compiled single-pass kernel (both directions) for transform length n.
@@ -108,8 +109,10 @@ cudaError_t prepare_rows(const RowsVariant& v);
 
 // Launch a rows variant over `batch` contiguous rows.  `grid_cap` bounds the
 // grid of a persistent variant (see persistent_grid); ignored otherwise.
+// `status` receives bounded-wait timeouts of the TMA variants (may be null
+// for the others).
 cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, float2* out, const float2* tw,
-                        long long batch, int grid_cap, cudaStream_t stream);
+                        long long batch, int grid_cap, cudaStream_t stream, int* status = nullptr);
 
 // tw[j] = exp(-2*pi*i*j/n) for j < n, evaluated in FP64 on the device.
 cudaError_t launch_twiddle_table(float2* tw, int64_t n, cudaStream_t stream);

@@ -27,9 +27,11 @@ static const RowsVariant kMixed[] = {
     GBFFT_ROWS_T(768, 192, 4, 4, 3, 16, 16),
     GBFFT_ROWS(768, 24, 2, 4, 3, 8, 8, 4),
     GBFFT_ROWS_T(1536, 192, 2, 4, 3, 16, 16, 2),
+    GBFFT_ROWS_TMA(1536, 192, 2, 4, 3, 16, 16, 2),
     GBFFT_ROWS_T(1536, 192, 4, 4, 3, 16, 32),
     GBFFT_ROWS(1536, 24, 2, 4, 3, 8, 8, 8),
     GBFFT_ROWS_T(3072, 192, 1, 4, 3, 16, 16, 4),
+    GBFFT_ROWS_TMA(3072, 192, 1, 4, 3, 16, 16, 4),
     GBFFT_ROWS_T(3072, 192, 2, 4, 3, 16, 32, 2),
     GBFFT_ROWS_T(3072, 192, 2, 4, 3, 32, 32),
     GBFFT_ROWS(5, 5, 128, 0, 5),
@@ -50,6 +52,7 @@ static const RowsVariant kMixed[] = {
     GBFFT_ROWS_T(1280, 160, 2, 5, 5, 16, 16),
     GBFFT_ROWS(1280, 40, 2, 4, 5, 8, 8, 4),
     GBFFT_ROWS_T(2560, 160, 1, 5, 5, 16, 16, 2),
+    GBFFT_ROWS_TMA(2560, 160, 1, 5, 5, 16, 16, 2),
     GBFFT_ROWS_T(2560, 160, 2, 4, 5, 16, 32),
     GBFFT_ROWS(2560, 40, 2, 4, 5, 8, 8, 8),
     GBFFT_ROWS(7, 7, 128, 0, 7),
@@ -70,6 +73,7 @@ static const RowsVariant kMixed[] = {
     GBFFT_ROWS_T(1792, 224, 2, 4, 7, 16, 16),
     GBFFT_ROWS(1792, 56, 2, 4, 7, 8, 8, 4),
     GBFFT_ROWS_T(3584, 224, 1, 4, 7, 16, 16, 2),
+    GBFFT_ROWS_TMA(3584, 224, 1, 4, 7, 16, 16, 2),
     GBFFT_ROWS_T(3584, 224, 2, 4, 7, 16, 32),
     GBFFT_ROWS(3584, 56, 2, 4, 7, 8, 8, 8),
 };

@@ -31,10 +31,12 @@ static const RowsVariant kPow2[] = {
     GBFFT_ROWS(1024, 16, 2, 4, 16, 16, 4),
     GBFFT_ROWS_PF(1024, 16, 2, 4, 16, 16, 4),
     GBFFT_ROWS(2048, 16, 1, 4, 16, 16, 8),
+    GBFFT_ROWS_TMA(2048, 128, 1, 4, 16, 16, 8),
     GBFFT_ROWS(2048, 64, 2, 4, 32, 64),
     GBFFT_ROWS(2048, 16, 2, 4, 8, 16, 16),
     GBFFT_ROWS_PF(2048, 16, 2, 4, 16, 16, 8),
     GBFFT_ROWS(4096, 16, 1, 4, 16, 16, 16),
+    GBFFT_ROWS_TMA(4096, 256, 1, 4, 16, 16, 16),
     GBFFT_ROWS(4096, 64, 1, 4, 64, 64),
     GBFFT_ROWS(4096, 64, 2, 4, 64, 64),
     GBFFT_ROWS_PF(4096, 16, 1, 4, 16, 16, 16),

@@ -132,6 +132,7 @@ struct Server {
     std::unique_ptr<Arena> arena;
     std::vector<cudaStream_t> streams;
     cudaStream_t tstream = nullptr;  // plan tables are built here, off the serving streams
+    int* status = nullptr;           // device status word for bounded waits of the kernels
     int next_stream = 0;
     std::map<std::pair<int64_t, int>, ServerPlan> plans;
 
@@ -172,7 +173,7 @@ gbfft_status get_plan(Server* s, int64_t n, int dir, ServerPlan** out) {
     if (rows_variants_for(n, cands, 1) > 0) {
         sp.rv = cands[0];
         if (prepare_rows(*sp.rv) != cudaSuccess) return GBFFT_ERR_CUDA;
-        if (sp.rv->kind == kRowsPersistent) sp.grid_cap = persistent_grid(*sp.rv);
+        if (sp.rv->kind == kRowsPersistent || sp.rv->kind == kRowsTma) sp.grid_cap = persistent_grid(*sp.rv);
         const int cnt = stage_twiddle_count(sp.rv->radix, sp.rv->nstages);
         if (cudaMalloc(&sp.tw, sizeof(float2) * (size_t)std::max(cnt, 1)) != cudaSuccess) return GBFFT_ERR_OOM;
         if (launch_stage_twiddles(sp.tw, n, sp.rv->radix, sp.rv->nstages, s->tstream) != cudaSuccess) return GBFFT_ERR_CUDA;
@@ -226,8 +227,8 @@ bool launch_group(Server* s, Group* g, ServerPlan* sp, int64_t n, int dir, int64
         at += row_bytes * (size_t)r->batch;
     }
     if (!sp->two_pass) {
-        ok = ok && launch_rows(*sp->rv, dir, data, data, sp->tw, (long long)rows, sp->grid_cap, g->stream) ==
-                       cudaSuccess;
+        ok = ok && launch_rows(*sp->rv, dir, data, data, sp->tw, (long long)rows, sp->grid_cap, g->stream,
+                               s->status) == cudaSuccess;
     } else {
         float2* ws = (float2*)((char*)data + ((row_bytes * (size_t)rows + 255) & ~size_t(255)));
         ok = ok && launch_cols(*sp->cm, 1, dir, data, ws, sp->tw_m, sp->post, (long long)rows, (int)sp->k,
@@ -369,6 +370,12 @@ gbfft_status server_create(Server** out, size_t budget, int n_streams, int flags
         return GBFFT_ERR_OOM;
     }
     s->arena.reset(new Arena(budget));
+    if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess || cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(s->arena_base);
+        delete s;
+        return GBFFT_ERR_OOM;
+    }
     if (cudaStreamCreateWithFlags(&s->tstream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaFree(s->arena_base);
         delete s;
@@ -531,6 +538,7 @@ void server_destroy(Server* s) {
             if (b) cudaFree(b);
     }
     cudaFree(s->arena_base);
+    cudaFree(s->status);
     delete s;
 }
 

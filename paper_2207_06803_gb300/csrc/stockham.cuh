@@ -34,7 +34,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "codelets.cuh"
+#include "gbfft.h"
 
 namespace gbfft {
 
@@ -258,6 +261,132 @@ __global__ void __launch_bounds__(T * N / E) k_stockham_rows_pf(const float2* in
             gather_global<N, E, T, R1>(nxt, ContigIO<N>{in + next * T * N, nullptr}, tile_rows(next, T, batch));
         run_stages<N, S, E, T, PS, true, 0, 1, Rs...>(v, ContigIO<N>{nullptr, out + tile * T * N}, sm, tw,
                                                       tile_rows(tile, T, batch));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel with TMA prefetch.  Each CTA walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; while it transforms tile i from a shared-memory
+// staging buffer, the TMA engine already copies tile i + gridDim.x (one
+// contiguous block of T rows) into the other staging buffer with a 1-D bulk
+// copy (cp.async.bulk) that completes on an mbarrier.  Stage 1 then reads the
+// staged tile, the stages exchange through the padded buffer as usual, and the
+// last stage writes HBM directly.  Every wait on an mbarrier is bounded (a
+// globaltimer deadline); on expiry the kernel records GBFFT_ERR_TIMEOUT in the
+// status word, waits (bounded again) for its copies in flight and returns.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long gbfft_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+    const uint32_t addr = smem_u32(bar);
+    const unsigned long long t0 = gbfft_globaltimer();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n"
+            "}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (gbfft_globaltimer() - t0 > limit_ns) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16),
+// completing `bytes` of transaction count on `bar`.
+__device__ __forceinline__ void tma_load_1d(void* dst_smem, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst_smem)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;  // 1 s bound on any copy wait
+
+template <int N, int T, int PS>
+constexpr int tma_smem_bytes() {
+    return 2 * T * N * (int)sizeof(float2) + smem_elems<T, N, PS>() * (int)sizeof(float2) + 16;
+}
+
+template <int N, int S, int TPB, int T, int PS, int... Rs>
+__global__ void __launch_bounds__(TPB) k_stockham_rows_tma(const float2* in, float2* out,
+                                                            const float2* __restrict__ tw, long long batch,
+                                                            int* status) {
+    constexpr int E = capacity_of_r<N, T, TPB, Rs...>();
+    extern __shared__ __align__(128) float2 smem_all[];
+    float2* const stage0 = smem_all;
+    float2* const stage1 = smem_all + T * N;
+    float2* xbuf = smem_all + 2 * T * N;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(xbuf + smem_elems<T, N, PS>());
+    const long long ntiles = (batch + T - 1) / T;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    long long tile = blockIdx.x;
+    if (tid == 0 && tile < ntiles) {
+        const uint32_t bytes = (uint32_t)(tile_rows(tile, T, batch) * N * sizeof(float2));
+        mbar_expect_tx(&bars[0], bytes);
+        tma_load_1d(stage0, in + tile * T * N, bytes, &bars[0]);
+    }
+    uint32_t phase0 = 0u, phase1 = 0u;
+    for (int i = 0; tile < ntiles; tile += gridDim.x, ++i) {
+        const int b = i & 1;
+        float2* const cur = b ? stage1 : stage0;
+        float2* const other = b ? stage0 : stage1;
+        __syncthreads();  // the other staging buffer and the exchange buffer are free again
+        const long long next = tile + gridDim.x;
+        if (tid == 0 && next < ntiles) {
+            const uint32_t bytes = (uint32_t)(tile_rows(next, T, batch) * N * sizeof(float2));
+            fence_proxy_async_smem();
+            mbar_expect_tx(&bars[b ^ 1], bytes);
+            tma_load_1d(other, in + next * T * N, bytes, &bars[b ^ 1]);
+        }
+        const uint32_t par = b ? phase1 : phase0;
+        const int ok = __syncthreads_and(mbar_wait(&bars[b], par, kTmaWaitNs) ? 1 : 0);
+        if (!ok) {  // uniform decision: every thread leaves together
+            if (tid == 0) atomicCAS(status, 0, (int)GBFFT_ERR_TIMEOUT);
+            if (next < ntiles) mbar_wait(&bars[b ^ 1], b ? phase0 : phase1, kTmaWaitNs);
+            return;
+        }
+        if (b) phase1 ^= 1u;
+        else phase0 ^= 1u;
+        const int nvalid = tile_rows(tile, T, batch);
+        float2 v[E];
+        gather_global<N, E, T, First<Rs...>::value, ContigIO<N>, TPB>(v, ContigIO<N>{cur, nullptr}, nvalid);
+        run_stages_t<N, S, E, T, PS, TPB, true, 0, 1, Rs...>(v, ContigIO<N>{nullptr, out + tile * T * N}, xbuf, tw,
+                                                            nvalid);
     }
 }
 

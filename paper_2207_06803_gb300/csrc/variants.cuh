@@ -55,6 +55,23 @@ inline RowsVariant make_rows_t_variant() {
                        (const void*)&k_stockham_rows_t<N, +1, TPB, T, PS, Rs...>};
 }
 
+template <int N, int TPB, int T, int PS, int... Rs>
+inline RowsVariant make_rows_tma_variant() {
+    static_assert(((Rs * ...) == N), "radix schedule must multiply to N");
+    static_assert((T * N) % 2 == 0, "bulk copies move whole 16-byte units");
+    return RowsVariant{kRowsTma,
+                       N,
+                       capacity_of_r<N, T, TPB, Rs...>(),
+                       T,
+                       TPB,
+                       PS,
+                       (int)sizeof...(Rs),
+                       {Rs...},
+                       tma_smem_bytes<T, N, PS>(),
+                       (const void*)&k_stockham_rows_tma<N, -1, TPB, T, PS, Rs...>,
+                       (const void*)&k_stockham_rows_tma<N, +1, TPB, T, PS, Rs...>};
+}
+
 template <int N, int T>
 inline RowsVariant make_small_variant() {
     return RowsVariant{kRowsSmall,
@@ -76,3 +93,4 @@ inline RowsVariant make_small_variant() {
 #define GBFFT_ROWS_PF(N, E, T, PS, ...) ::gbfft::make_rows_pf_variant<N, E, T, PS, __VA_ARGS__>()
 #define GBFFT_SMALL(N, T) ::gbfft::make_small_variant<N, T>()
 #define GBFFT_ROWS_T(N, TPB, T, PS, ...) ::gbfft::make_rows_t_variant<N, TPB, T, PS, __VA_ARGS__>()
+#define GBFFT_ROWS_TMA(N, TPB, T, PS, ...) ::gbfft::make_rows_tma_variant<N, TPB, T, PS, __VA_ARGS__>()

@@ -53,6 +53,42 @@ def test_every_variant_every_size(direction):
             check(gpu_fft(x, direction, variant=v), x, direction)
 
 
+def test_persistent_variants_walk_many_tiles():
+    """Persistent kernels (register prefetch, TMA bulk-copy prefetch) over
+    enough rows that every CTA walks several tiles, plus a ragged last tile:
+    bit-identical to the one-tile-per-CTA kernel with the same schedule, and
+    within tolerance of the oracle on sampled rows."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    checked = 0
+    for n in single_pass_sizes():
+        kinds = [gbfft.gbfft_variant_kind(n, v) for v in range(gbfft.gbfft_num_variants(n))]
+        for v, kind in enumerate(kinds):
+            if kind not in (1, 3):
+                continue
+            rad = gbfft.gbfft_variant_info(n, v)["radices"]
+            ref_v = next((w for w, k in enumerate(kinds) if k == 0 and gbfft.gbfft_variant_info(n, w)["radices"] == rad), None)
+            batch = (1 << 23) // n + 3
+            x = synth.uniform_batch(SEED + v, n, batch)
+            d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+            outs = []
+            for var in ([v] if ref_v is None else [v, ref_v]):
+                d_out = torch.full_like(d_in, float("nan"))
+                with gbfft.Plan(n, batch, -1, variant=var) as p:
+                    p.execute(d_in, d_out)
+                    torch.cuda.synchronize()
+                    assert gbfft.gbfft_plan_device_status(p.handle) == 0
+                outs.append(d_out)
+            if len(outs) == 2:
+                assert torch.equal(outs[0], outs[1]), (n, v, ref_v)
+            rows = synth.sample_rows(SEED, batch, 64)
+            rows = np.concatenate([rows, [batch - 1]])
+            y = outs[0].view(batch, 2 * n)[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.complex64)
+            check(y, x[rows], -1)
+            checked += 1
+    assert checked >= 4
+
+
 @pytest.mark.parametrize("n", [8, 64, 256, 1024, 4096, 96, 640, 3584])
 def test_in_place_equals_out_of_place(n):
     x = synth.uniform_batch(SEED, n, 37)
