@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="skip the short live runs of the two-pass, tensor-core, ragged and serving paths")
     ap.add_argument("--sizes", type=str, default=None,
                     help="comma-separated subset of the sweep (for small profiling cases)")
     ap.add_argument("--dtype", type=int, default=0,
@@ -87,10 +89,15 @@ def measured_peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def source_digest() -> str:
+# Files that define the single-pass rows kernels (the sweep's dominant kernel):
+# a recorded DRAM-traffic figure is valid only while these hash the same.
+ROWS_KERNEL_SOURCES = ("codelets.cuh", "stockham.cuh", "variants.cuh", "rows_pow2.cu")
+
+
+def source_digest(files=ROWS_KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_06803_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in files:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -385,6 +392,10 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(flat)
 
+    others = None
+    if rank == 0 and world == 1 and not args.no_other_configs:
+        others = other_configs(args)
+
     value = world * args.steps * calls * BYTES_PER_CALL / (max_ms * 1e-3) / 1e9
     if rank == 0:
         line = {
@@ -401,6 +412,7 @@ def run_gpu(args):
             "frac_of_hbm_per_size": {k: {kk: vv / peak for kk, vv in v.items()} for k, v in per_size.items()},
             "roundtrip_rel_l2_max": roundtrip,
             "gpu": torch.cuda.get_device_name(),
+            "other_configs": others,
         }
         print(json.dumps(line), flush=True)
     for _, p in plans:
@@ -409,6 +421,36 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def other_configs(args):
+    """Short live runs of the other hot-path rows, summarised (errors recorded, never fatal)."""
+    out = {}
+    small = argparse.Namespace(**vars(args))
+    small.steps = 40
+    for name, fn in (("twopass", run_twopass), ("tc", lambda a: run_tc(a, dists=("uniform",))),
+                     ("ragged", run_ragged),
+                     ("serving", lambda a: run_serving(a, rates=(1000, 10000), scale=0.2, serial_rates=(1000,)))):
+        try:
+            r = fn(small)
+        except Exception as e:  # a failing secondary measurement must not lose the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        if name == "twopass":
+            out[name] = {n: round(v["alg_gbs"], 1) for n, v in r["per_size"].items()}
+        elif name == "tc":
+            out[name] = {k: {"gbs": round(v["gbs"], 1), "vs_fp32": round(v["vs_fp32"], 3),
+                             "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for k, v in r["results"].items()}
+        elif name == "ragged":
+            res = r["results"]
+            out[name] = {k: res[k] for k in ("ragged_graph_tuned_us", "ragged_gbs", "per_size_us", "per_transform_us",
+                                             "speedup_vs_per_size", "speedup_vs_per_transform", "items")}
+        else:
+            out[name] = {"batching": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s", "gb_per_s")}
+                                      for rate, v in r["batching"].items()},
+                         "serial_queue": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s")}
+                                          for rate, v in r["serial_queue"].items()}}
+    return out
 
 
 def run_e2e(torch, np, flat, plans, stream, world, e2e_steps, calls):
@@ -482,13 +524,11 @@ def run_twopass(args):
         alg = BYTES_PER_CALL / (ms * 1e-3) / 1e9
         rows[str(n)] = {"k_outer": info["k_outer"], "m_inner": info["m_inner"], "ms": ms, "alg_gbs": alg,
                         "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak}
-    print(json.dumps({"config": "twopass", "metric": "two-pass Eq. 2 c2c GB/s (16 B/point algorithmic)",
-                      "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src,
-                      "per_size": rows}), flush=True)
-    return 0
+    return {"config": "twopass", "metric": "two-pass Eq. 2 c2c GB/s (16 B/point algorithmic)",
+            "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_size": rows}
 
 
-def run_tc(args):
+def run_tc(args, dists=("uniform", "gaussian_scaled")):
     """Tensor-core split precision vs the plain FP32 kernel: N=256 (2^18 rows), N=4096 (2^14 rows)."""
     import numpy as np
     import torch
@@ -497,7 +537,7 @@ def run_tc(args):
     stream = torch.cuda.current_stream()
     peak, src = _peak()
     out = {}
-    for n, dist in ((256, "uniform"), (4096, "uniform"), (256, "gaussian_scaled"), (4096, "gaussian_scaled")):
+    for n, dist in [(n, d) for d in dists for n in (256, 4096)]:
         batch = TOTAL // n
         x = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL) if dist == "uniform" else \
             synth.gaussian_scaled_batch(synth.DEFAULT_SEED, n, batch).reshape(-1)
@@ -518,10 +558,8 @@ def run_tc(args):
     for key in list(out):
         n, dist, name = key.split("/")
         out[key]["vs_fp32"] = out[key]["gbs"] / out[f"{n}/{dist}/fp32"]["gbs"]
-    print(json.dumps({"config": "tc", "metric": "tensor-core split-precision c2c GB/s vs plain FP32",
-                      "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src,
-                      "results": out}), flush=True)
-    return 0
+    return {"config": "tc", "metric": "tensor-core split-precision c2c GB/s vs plain FP32",
+            "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "results": out}
 
 
 def run_ragged(args):
@@ -591,12 +629,10 @@ def run_ragged(args):
         p.close()
     res["speedup_vs_per_size"] = ms2 / ms1
     res["speedup_vs_per_transform"] = ms3 / ms1
-    print(json.dumps({"config": "ragged", "metric": "ragged batch GB/s on sum(16*N_i)", "unit": "GB/s",
-                      "results": res}), flush=True)
-    return 0
+    return {"config": "ragged", "metric": "ragged batch GB/s on sum(16*N_i)", "unit": "GB/s", "results": res}
 
 
-def run_serving(args):
+def run_serving(args, rates=(1000, 2000, 5000, 10000, 20000, 50000), scale=1.0, serial_rates=(1000, 5000)):
     """Open-loop Poisson arrivals; each request batch ~ U{1..256}, N uniform over
     {2^k,3*2^k,5*2^k,7*2^k} in [16, 16384]; 4 GiB budget; continuous batching vs the serial queue."""
     import numpy as np
@@ -614,7 +650,6 @@ def run_serving(args):
         t_in.append(torch.from_numpy(x.view(np.float32)).pin_memory())
         t_out.append(torch.empty_like(t_in[-1]).pin_memory())
     budget = 4 << 30
-    rates = [1000, 2000, 5000, 10000, 20000, 50000]
     results = {}
 
     def drive(srv, rate, count, seed):
@@ -637,7 +672,7 @@ def run_serving(args):
             srv.prepare(int(n), -1)
         drive(srv, 5000, 1000, 7)  # warm-up
         for rate in rates:
-            count = 20000 if rate >= 5000 else 10 * rate // 1000 * 1000
+            count = max(500, int(scale * (20000 if rate >= 5000 else 10 * rate)))
             st = drive(srv, rate, count, rate)
             results[str(rate)] = dict(st, requests=count, offered_req_per_s=rate)
     serial = {}
@@ -645,13 +680,13 @@ def run_serving(args):
         for n in fam.tolist():
             srv.prepare(int(n), -1)
         drive(srv, 1000, 500, 8)
-        for rate in (1000, 5000):
-            st = drive(srv, rate, 3000, rate + 1)
-            serial[str(rate)] = dict(st, requests=3000, offered_req_per_s=rate)
-    print(json.dumps({"config": "serving", "metric": "serving p50/p99 latency (s) and throughput",
-                      "budget_bytes": budget, "streams": 4, "request_templates": templates,
-                      "batching": results, "serial_queue": serial}), flush=True)
-    return 0
+        for rate in serial_rates:
+            count = max(500, int(scale * 3000))
+            st = drive(srv, rate, count, rate + 1)
+            serial[str(rate)] = dict(st, requests=count, offered_req_per_s=rate)
+    return {"config": "serving", "metric": "serving p50/p99 latency (s) and throughput",
+            "budget_bytes": budget, "streams": 4, "request_templates": templates,
+            "batching": results, "serial_queue": serial}
 
 
 def main():
@@ -659,7 +694,9 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "sweep":
-        return {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving}[args.config](args)
+        fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving}[args.config]
+        print(json.dumps(fn(args)), flush=True)
+        return 0
     return run_gpu(args)
 
 
