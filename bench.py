@@ -544,8 +544,9 @@ def run_tc(args, dists=("uniform", "gaussian_scaled")):
         d_in = torch.from_numpy(x.view(np.float32)).cuda()
         d_out = torch.empty_like(d_in)
         d_rt = torch.empty_like(d_in)
-        for name, dt in (("fp32", 0), ("fp16x2", 1), ("bf16x2", 2)):
-            with gbfft.Plan(n, batch, -1, dt) as pf, gbfft.Plan(n, batch, 1, dt) as pi:
+        for name, dt, var in (("fp32", 0, None), ("fp16x2", 1, 0), ("bf16x2", 2, 0), ("fp16x2_tcgen05", 1, 1),
+                              ("bf16x2_tcgen05", 2, 1)):
+            with gbfft.Plan(n, batch, -1, dt, variant=var) as pf, gbfft.Plan(n, batch, 1, dt, variant=var) as pi:
                 ms = _time_ms(torch, lambda: pf.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
                 pi.execute(d_out, d_rt, stream)
                 torch.cuda.synchronize()

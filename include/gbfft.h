@@ -85,7 +85,11 @@ int gbfft_version(void);
  * product on the tensor cores with both operands split into high and low
  * half-precision parts (Mh Xh + Mh Xl + Ml Xh, FP32 accumulation); FP16
  * columns are scaled by exact powers of two first.  Stage twiddles stay FP32.
- * The variant and two-pass forms are FP32-only (INVALID_ARG otherwise).
+ * gbfft_plan_create_variant with a tensor-core dtype selects the engine:
+ * variant 0 (default) issues warp-level mma.sync.m16n8k16 on register
+ * fragments; variant 1 (N = 256, 4096) issues tcgen05.mma from shared-memory
+ * operands into tensor memory and reads results back with tcgen05.ld.  The
+ * two-pass form is FP32-only (INVALID_ARG otherwise).
  */
 gbfft_status gbfft_plan_create(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype);
 

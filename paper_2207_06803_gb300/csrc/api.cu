@@ -83,8 +83,10 @@ struct gbfft_plan_s {
     RaggedState* ragged = nullptr;
     // tensor-core split precision (all-radix-16 schedule)
     const TcVariant* tcv = nullptr;
+    const UmmaVariant* umv = nullptr;  // tcgen05 engine (variant 1) instead of mma.sync (variant 0)
     int tc_prec = 0;
     uint32_t* tc_frag = nullptr;
+    uint16_t* umma_b = nullptr;
     int* status = nullptr;
     size_t ws_bytes = 0;
     // host-buffer execution: staging ring and its streams/events (created on first use)
@@ -126,6 +128,7 @@ void free_plan(gbfft_plan p) {
     if (p->s_out) cudaStreamDestroy(p->s_out);
     if (p->ragged) ragged_destroy(p->ragged);
     if (p->tc_frag) cudaFree(p->tc_frag);
+    if (p->umma_b) cudaFree(p->umma_b);
     float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
     for (float2* b : bufs)
         if (b) cudaFree(b);
@@ -165,9 +168,11 @@ gbfft_status alloc_stage_tables(float2** dst, int64_t n, const int* radix, int n
     return launch_stage_twiddles(*dst, n, radix, nstages, 0) == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
-gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype) {
+gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int engine) {
     const TcVariant* tv = tc_variant_for(n);
     if (!tv) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    const UmmaVariant* uv = engine == 1 ? umma_variant_for(n) : nullptr;
+    if (engine == 1 && !uv) return GBFFT_ERR_NOT_FOUND;
     // BF16x2 keeps ~17 significand bits; a lone radix-16 stage then errs by ~5e-6
     // relative L2, above the 1e-6*log2(N) = 4e-6 contract at N = 16.
     if (dtype == GBFFT_C2C_F32_TC_BF16X2 && n < 256) return GBFFT_ERR_UNSUPPORTED_SIZE;
@@ -179,6 +184,7 @@ gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction,
     p->direction = direction;
     p->dtype = dtype;
     p->tcv = tv;
+    p->umv = uv;
     p->tc_prec = dtype == GBFFT_C2C_F32_TC_FP16X2 ? 0 : 1;
     int radix[kMaxStages];
     for (int s = 0; s < tv->nstages; ++s) radix[s] = 16;
@@ -188,8 +194,18 @@ gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction,
         cudaGetLastError();
         st = GBFFT_ERR_OOM;
     }
-    if (st == GBFFT_OK && prepare_tc(*tv) != cudaSuccess) st = GBFFT_ERR_CUDA;
-    if (st == GBFFT_OK && (p->grid_cap = tc_grid(*tv)) <= 0) st = GBFFT_ERR_CUDA;
+    if (uv) {
+        if (st == GBFFT_OK && prepare_umma(*uv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+        if (st == GBFFT_OK && (p->grid_cap = umma_grid(*uv)) <= 0) st = GBFFT_ERR_CUDA;
+        if (st == GBFFT_OK && cudaMalloc(&p->umma_b, 64 * 32 * 2) != cudaSuccess) {
+            cudaGetLastError();
+            st = GBFFT_ERR_OOM;
+        }
+        if (st == GBFFT_OK && launch_umma_bmat(p->umma_b, p->tc_prec, direction, 0) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    } else {
+        if (st == GBFFT_OK && prepare_tc(*tv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+        if (st == GBFFT_OK && (p->grid_cap = tc_grid(*tv)) <= 0) st = GBFFT_ERR_CUDA;
+    }
     if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw, n, radix, tv->nstages);
     if (st == GBFFT_OK && launch_tc_fragments(p->tc_frag, p->tc_prec, direction, 0) != cudaSuccess)
         st = GBFFT_ERR_CUDA;
@@ -211,8 +227,9 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     if (dtype != GBFFT_C2C_F32 && dtype != GBFFT_C2C_F32_TC_FP16X2 && dtype != GBFFT_C2C_F32_TC_BF16X2)
         return GBFFT_ERR_INVALID_ARG;
     if (dtype != GBFFT_C2C_F32) {
-        if (variant >= 0 || k_outer > 0) return GBFFT_ERR_INVALID_ARG;
-        return create_tc(out, n, batch, direction, dtype);
+        if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
+        if (variant > 1) return GBFFT_ERR_NOT_FOUND;
+        return create_tc(out, n, batch, direction, dtype, variant < 0 ? 0 : variant);
     }
 
     const RowsVariant* cands[kMaxVariantsPerSize];
@@ -281,6 +298,9 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
 
 // Enqueue the transform of `rows` rows from `in` to `out` (device pointers).
 cudaError_t run_device(gbfft_plan p, const float2* in, float2* out, int64_t rows, cudaStream_t s) {
+    if (p->kind == kPlanTensorCore && p->umv)
+        return launch_umma(*p->umv, p->tc_prec, p->direction, in, out, p->tw, p->umma_b, (long long)rows,
+                           p->grid_cap, p->status, s);
     if (p->kind == kPlanTensorCore)
         return launch_tc(*p->tcv, p->tc_prec, p->direction, in, out, p->tw, p->tc_frag, (long long)rows,
                          p->grid_cap, s);
@@ -438,7 +458,7 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     if (nstages) *nstages = ns < kMaxStages ? ns : kMaxStages;
     if (radices)
         for (int i = 0; i < ns && i < kMaxStages; ++i) radices[i] = rad[i];
-    if (variant) *variant = p->kind == kPlanSingle ? p->variant : -1;
+    if (variant) *variant = p->kind == kPlanSingle ? p->variant : (p->kind == kPlanTensorCore ? (p->umv ? 1 : 0) : -1);
     if (workspace_bytes) *workspace_bytes = p->ws_bytes;
     return GBFFT_OK;
 }

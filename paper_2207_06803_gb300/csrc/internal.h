@@ -75,6 +75,21 @@ int tc_grid(const TcVariant& v);
 cudaError_t launch_tc(const TcVariant& v, int prec, int direction, const float2* in, float2* out, const float2* tw,
                       const uint32_t* frag, long long batch, int grid_cap, cudaStream_t s);
 
+// Tensor-core variant on tcgen05 / tensor memory (umma.cu): same schedules
+// and arithmetic as the mma.sync variant; N = 256 and 4096.
+struct UmmaVariant {
+    int n, rows, tpb, smem;
+    const void* k[2][2];  // [prec][dir]
+};
+const UmmaVariant* umma_variant_for(int64_t n);
+cudaError_t prepare_umma(const UmmaVariant& v);
+int umma_grid(const UmmaVariant& v);
+// bm: 64 x 32 halves (4 KB) of [Mh; Ml] in the operand layout the kernel expects.
+cudaError_t launch_umma_bmat(uint16_t* bm, int prec, int sign, cudaStream_t s);
+cudaError_t launch_umma(const UmmaVariant& v, int prec, int direction, const float2* in, float2* out,
+                        const float2* tw, const void* bmat, long long batch, int grid_cap, int* status,
+                        cudaStream_t s);
+
 // Ragged-batch plans (ragged.cu).
 struct RaggedState;
 gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* offsets, int64_t count);

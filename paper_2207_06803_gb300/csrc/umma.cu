@@ -1,0 +1,406 @@
+// Tensor-core variant on the fifth-generation tensor cores (tcgen05, TMEM).
+//
+// Same arithmetic as tc.cu (every radix-16 stage's DFT_16 as the real product
+// [yr; yi] = M [xr; xi], M = [[Fr, -Fi], [Fi, Fr]], with operands split into
+// high and low half-precision parts, Mh Xh + Mh Xl + Ml Xh, FP32 accumulation),
+// arranged for tcgen05.mma instead of warp-level mma.sync:
+//   - one thread per butterfly (column of 16 complex), exactly as the FP32
+//     Stockham engine: it loads its column, applies the FP32 stage twiddles,
+//     scales by an exact power of two (FP16), splits into hi/lo and writes
+//     the column as one 32-element row of the A operands Ah = Xh^T and
+//     Al = Xl^T (128 rows per MMA tile) in shared memory;
+//   - B = [Mh; Ml]^T is resident in shared memory for the whole kernel;
+//   - one elected thread issues D = Ah [Mh | Ml]^T (N = 64) and D[:, 0:32] +=
+//     Al Mh^T (N = 32), each as two K = 16 instructions, and commits them to an
+//     mbarrier; D (128 lanes x 64 FP32 columns) lives in tensor memory;
+//   - each warp reads back its own 32 TMEM lanes (its own 32 butterflies) with
+//     tcgen05.ld and forms y = D[:, 0:32] + D[:, 32:64], then writes the 16
+//     outputs with the Stockham pattern (shared-memory exchange or HBM).
+// Operand layout: K-major, no swizzle; a core matrix is 8 rows x 16 bytes
+// (8 halves of K), core matrices adjacent in K are 128 bytes apart (leading
+// byte offset) and 8-row groups 512 bytes apart (stride byte offset).
+// Every wait is bounded (globaltimer deadline); on expiry the kernel records
+// GBFFT_ERR_TIMEOUT, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "stockham.cuh"
+
+namespace gbfft {
+namespace {
+
+constexpr unsigned long long kUmmaWaitNs = 1000000000ull;
+constexpr int kRowBytes = 64;    // one 32-element K row of halves
+constexpr int kLbo = 128;        // K-adjacent core matrices
+constexpr int kSbo = 512;        // 8-row groups (4 core matrices of K)
+constexpr int kTileBytes = 128 * kRowBytes;  // one 128 x 32 operand
+
+__device__ __forceinline__ uint32_t a_offset(int row, int kgroup) {
+    return (uint32_t)((row >> 3) * kSbo + kgroup * kLbo + (row & 7) * 16);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 [0,14), leading byte
+// offset >> 4 [16,30), stride byte offset >> 4 [32,46), fixed version 1
+// [46,48), base offset 0, no swizzle (layout type 0 in [61,64)).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((kLbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((kSbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator [4,6) = 1, A/B format
+// [7,10) / [10,13) (0 = F16, 1 = BF16), both K-major, N >> 3 at [17,23),
+// M >> 4 at [24,29).
+__host__ __device__ constexpr uint32_t instr_desc(int prec, int m, int n) {
+    return (1u << 4) | ((uint32_t)prec << 7) | ((uint32_t)prec << 10) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 columns of 32-bit values starting at column `col` of this
+// warp's TMEM sub-partition; thread i gets lane i.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack_hi(float a, float b, float& ra, float& rb) {
+    if constexpr (PREC == 0) {
+        const __half2 h = __floats2half2_rn(a, b);
+        const float2 f = __half22float2(h);
+        ra = a - f.x;
+        rb = b - f.y;
+        return *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        const float2 f = __bfloat1622float2(h);
+        ra = a - f.x;
+        rb = b - f.y;
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack_lo(float a, float b) {
+    if constexpr (PREC == 0) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
+struct UmmaShared {
+    uint8_t* a_hi;       // MT tiles of 128 x 32
+    uint8_t* a_lo;
+    uint8_t* b;          // [Mh; Ml] as 64 rows x 32 (K-major)
+    float2* xbuf;        // padded exchange buffer
+    uint64_t* bar;       // MMA completion
+    uint32_t* tmem_slot; // TMEM base address written by tcgen05.alloc
+};
+
+// One radix-16 stage: threads own butterflies B = tid (MT*128 of them).
+template <int N, int S, int PREC, int T, int PS, int L, bool FIRST, bool LAST>
+__device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShared& sh, uint32_t tmem,
+                                           const float2* __restrict__ tw, int nvalid, uint32_t& phase) {
+    constexpr int R = 16, NR = N / R;
+    const int tid = threadIdx.x;
+    const int B = tid;
+    const int t = B / NR, j = B % NR, k = j % L;
+    float2 x[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int n = j + q * NR;
+        if constexpr (FIRST) {
+            x[q] = (t < nvalid) ? io.ld(t, n) : make_float2(0.f, 0.f);
+        } else {
+            x[q] = sh.xbuf[spad<PS>(t * N + n)];
+        }
+        if constexpr (L > 1) {
+            if (q > 0) x[q] = twiddle<S>(x[q], __ldg(&tw[(q - 1) * L + k]));
+        }
+    }
+    float inv_sc = 1.f;
+    if constexpr (PREC == 0) {
+        float m = 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) m = fmaxf(m, fmaxf(fabsf(x[q].x), fabsf(x[q].y)));
+        int e = (int)((__float_as_uint(m) >> 23) & 0xff) - 127;
+        if (!(m > 0.f)) e = 0;
+        e = max(-100, min(100, e));
+        const float sc = __uint_as_float((uint32_t)(127 + 14 - e) << 23);
+        inv_sc = __uint_as_float((uint32_t)(127 - 14 + e) << 23);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) x[q] = make_float2(x[q].x * sc, x[q].y * sc);
+    }
+    // Row B of Ah / Al: K index 0..15 = real parts (q), 16..31 = imaginary parts.
+    {
+        const int mt = B >> 7, row = B & 127;
+        uint8_t* ah = sh.a_hi + mt * kTileBytes;
+        uint8_t* al = sh.a_lo + mt * kTileBytes;
+#pragma unroll
+        for (int kg = 0; kg < 4; ++kg) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int kk = kg * 8 + 2 * p;  // K index of the pair's first element
+                const float a0 = kk < 16 ? x[kk].x : x[kk - 16].y;
+                const float a1 = kk < 16 ? x[kk + 1].x : x[kk - 15].y;
+                float r0, r1;
+                h[p] = pack_hi<PREC>(a0, a1, r0, r1);
+                l[p] = pack_lo<PREC>(r0, r1);
+            }
+            *reinterpret_cast<uint4*>(ah + a_offset(row, kg)) = make_uint4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<uint4*>(al + a_offset(row, kg)) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    constexpr int MT = T * N / 16 / 128;
+    if (tid == 0) {
+        const uint32_t idesc64 = instr_desc(PREC, 128, 64), idesc32 = instr_desc(PREC, 128, 32);
+        const uint32_t b_addr = smem_u32(sh.b);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            const uint32_t d = tmem + (uint32_t)(mt * 64);
+            const uint32_t ah = smem_u32(sh.a_hi + mt * kTileBytes), al = smem_u32(sh.a_lo + mt * kTileBytes);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)  // D = Ah [Mh | Ml]^T
+                umma_f16(d, smem_desc(ah + ks * 2 * kLbo), smem_desc(b_addr + ks * 2 * kLbo), idesc64, ks);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)  // D[:, 0:32] += Al Mh^T
+                umma_f16(d, smem_desc(al + ks * 2 * kLbo), smem_desc(b_addr + ks * 2 * kLbo), idesc32, 1);
+        }
+        umma_commit(sh.bar);
+    }
+    const int ok = __syncthreads_and(mbar_wait(sh.bar, phase, kUmmaWaitNs) ? 1 : 0);
+    phase ^= 1u;
+    if (!ok) return false;
+    tc_fence_after();
+    // Warp w reads TMEM lanes 32*(w%4) .. +31 of the D tile of its M-tile.
+    const int warp = tid >> 5;
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+    float d0[32], d1[32];
+    tmem_ld32(taddr, d0);
+    tmem_ld32(taddr + 32, d1);
+    float2 y[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) y[m] = make_float2((d0[m] + d1[m]) * inv_sc, (d0[16 + m] + d1[16 + m]) * inv_sc);
+    tc_fence_before();
+    if constexpr (!FIRST && !LAST) __syncthreads();  // every column of this stage has been read from xbuf
+    const int b = j / L;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        if constexpr (LAST) {
+            if (t < nvalid) io.st(t, m * L + j, y[m]);
+        } else {
+            sh.xbuf[spad<PS>(t * N + b * L * R + m * L + k)] = y[m];
+        }
+    }
+    if constexpr (!LAST) __syncthreads();
+    return true;
+}
+
+template <int N, int S, int PREC, int T, int PS, int L>
+__device__ __forceinline__ bool umma_stages(const ContigIO<N>& io, const UmmaShared& sh, uint32_t tmem,
+                                            const float2* __restrict__ tw, int nvalid, uint32_t& phase) {
+    constexpr bool LAST = (L * 16 == N);
+    if (!umma_stage<N, S, PREC, T, PS, L, L == 1, LAST>(io, sh, tmem, tw + (L > 1 ? L - 16 : 0), nvalid, phase))
+        return false;
+    if constexpr (!LAST) return umma_stages<N, S, PREC, T, PS, L * 16>(io, sh, tmem, tw, nvalid, phase);
+    return true;
+}
+
+// bmat: 64 x 32 halves in the K-major core-matrix layout (k_umma_bmat).
+template <int N, int S, int PREC, int T, int PS>
+__global__ void __launch_bounds__(T * N / 16) k_stockham_umma(const float2* in, float2* out,
+                                                               const float2* __restrict__ tw,
+                                                               const uint4* __restrict__ bmat, long long batch,
+                                                               int* status) {
+    constexpr int TPB = T * N / 16;
+    constexpr int MT = TPB / 128;
+    constexpr uint32_t kCols = MT == 1 ? 64 : 128;
+    static_assert(TPB % 128 == 0 && (MT == 1 || MT == 2), "one or two M = 128 tiles per stage");
+    extern __shared__ __align__(1024) uint8_t usm[];
+    UmmaShared sh;
+    sh.a_hi = usm;
+    sh.a_lo = usm + MT * kTileBytes;
+    sh.b = usm + 2 * MT * kTileBytes;
+    sh.xbuf = reinterpret_cast<float2*>(usm + 2 * MT * kTileBytes + 64 * kRowBytes);
+    sh.bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sh.xbuf) + smem_elems<T, N, PS>() * 8);
+    sh.tmem_slot = reinterpret_cast<uint32_t*>(sh.bar + 1);
+    const int tid = threadIdx.x;
+    // B operand, resident for the kernel (64 rows x 64 bytes = 256 uint4).
+    for (int i = tid; i < 64 * kRowBytes / 16; i += TPB) reinterpret_cast<uint4*>(sh.b)[i] = bmat[i];
+    if (tid == 0) {
+        mbar_init(sh.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sh.tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *sh.tmem_slot;
+    uint32_t phase = 0;
+    const long long ntiles = (batch + T - 1) / T;
+    bool ok = true;
+    for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        const int nvalid = tile_rows(tile, T, batch);
+        const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
+        ok = umma_stages<N, S, PREC, T, PS, 1>(io, sh, tmem, tw, nvalid, phase);
+    }
+    if (!ok && tid == 0) atomicCAS(status, 0, (int)GBFFT_ERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+// B = [Mh; Ml]: row n < 32 is Mh row n, row 32 + n is Ml row n, K-major
+// core-matrix layout; M[n][k] = [[Fr, -Fi], [Fi, Fr]][n][k] of
+// F = exp(sign * 2 pi i n q / 16), evaluated in FP64 and split hi/lo.
+__global__ void k_umma_bmat(uint16_t* bm, int prec, int sign) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;  // row * 32 + k
+    if (idx >= 64 * 32) return;
+    const int row = idx / 32, kk = idx % 32;
+    const int part = row / 32, n = row % 32;
+    const int m = n % 16, q = kk % 16;
+    const int e = (m * q) % 16;
+    double sn, cs;
+    sincospi(2.0 * (double)e / 16.0, &sn, &cs);
+    const double fr = cs, fi = (double)sign * sn;
+    double v;
+    if (n < 16) v = kk < 16 ? fr : -fi;
+    else v = kk < 16 ? fi : fr;
+    uint16_t bits;
+    if (prec == 0) {
+        const __half hi = __double2half(v);
+        const __half lo = __double2half(v - (double)__half2float(hi));
+        const __half pick = part == 0 ? hi : lo;
+        bits = *reinterpret_cast<const uint16_t*>(&pick);
+    } else {
+        const __nv_bfloat16 hi = __double2bfloat16(v);
+        const __nv_bfloat16 lo = __double2bfloat16(v - (double)__bfloat162float(hi));
+        const __nv_bfloat16 pick = part == 0 ? hi : lo;
+        bits = *reinterpret_cast<const uint16_t*>(&pick);
+    }
+    const uint32_t off = (uint32_t)((row >> 3) * kSbo + (kk >> 3) * kLbo + (row & 7) * 16 + (kk & 7) * 2);
+    bm[off / 2] = bits;
+}
+
+template <int N, int T, int PS>
+constexpr int umma_smem_bytes() {
+    return 2 * (T * N / 16 / 128) * kTileBytes + 64 * kRowBytes + smem_elems<T, N, PS>() * 8 + 16;
+}
+
+template <int N, int T, int PS>
+UmmaVariant make_umma_variant() {
+    UmmaVariant v{};
+    v.n = N;
+    v.rows = T;
+    v.tpb = T * N / 16;
+    v.smem = umma_smem_bytes<N, T, PS>();
+    v.k[0][0] = (const void*)&k_stockham_umma<N, -1, 0, T, PS>;
+    v.k[0][1] = (const void*)&k_stockham_umma<N, +1, 0, T, PS>;
+    v.k[1][0] = (const void*)&k_stockham_umma<N, -1, 1, T, PS>;
+    v.k[1][1] = (const void*)&k_stockham_umma<N, +1, 1, T, PS>;
+    return v;
+}
+
+const UmmaVariant kUmma[] = {
+    make_umma_variant<256, 8, 4>(),
+    make_umma_variant<4096, 1, 4>(),
+};
+
+}  // namespace
+
+const UmmaVariant* umma_variant_for(int64_t n) {
+    for (const UmmaVariant& v : kUmma)
+        if (v.n == n) return &v;
+    return nullptr;
+}
+
+cudaError_t prepare_umma(const UmmaVariant& v) {
+    for (int p = 0; p < 2; ++p)
+        for (int d = 0; d < 2; ++d) {
+            cudaError_t e = cudaFuncSetAttribute(v.k[p][d], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+int umma_grid(const UmmaVariant& v) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.k[0][0], v.tpb, (size_t)v.smem) != cudaSuccess)
+        return 0;
+    // Each CTA holds 64 or 128 TMEM columns of the SM's 512; stay well inside.
+    const int tmem_cap = 512 / (v.tpb > 128 ? 128 : 64);
+    if (per_sm > tmem_cap) per_sm = tmem_cap;
+    return per_sm * sms;
+}
+
+cudaError_t launch_umma_bmat(uint16_t* bm, int prec, int sign, cudaStream_t s) {
+    k_umma_bmat<<<8, 256, 0, s>>>(bm, prec, sign);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_umma(const UmmaVariant& v, int prec, int direction, const float2* in, float2* out,
+                        const float2* tw, const void* bmat, long long batch, int grid_cap, int* status,
+                        cudaStream_t s) {
+    if (batch <= 0) return cudaSuccess;
+    long long blocks = (batch + v.rows - 1) / v.rows;
+    if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
+    void* args[] = {(void*)&in, (void*)&out, (void*)&tw, (void*)&bmat, (void*)&batch, (void*)&status};
+    const void* fn = v.k[prec][direction == GBFFT_FORWARD ? 0 : 1];
+    return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.tpb), args, (size_t)v.smem, s);
+}
+
+}  // namespace gbfft

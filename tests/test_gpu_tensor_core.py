@@ -100,3 +100,30 @@ def test_tensor_core_in_place_and_host_pipeline():
         p.execute(d, d)
         torch.cuda.synchronize()
     assert torch.equal(d, ref) and torch.equal(h_out, ref.cpu())
+
+
+@pytest.mark.parametrize("dtype", list(DTYPES))
+@pytest.mark.parametrize("direction", [-1, 1])
+@pytest.mark.parametrize("n,batch", [(256, 2051), (4096, 137)])
+def test_tcgen05_engine_matches_gate_and_mma_sync(n, batch, direction, dtype):
+    """Variant 1 of the tensor-core dtypes runs the DFT_16 products with
+    tcgen05.mma into tensor memory; same split arithmetic as variant 0
+    (warp-level mma.sync), so both meet the gate and agree closely."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    x = synth.gaussian_scaled_batch(SEED + n, n, batch)
+    d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+    outs = []
+    for variant in (1, 0):
+        d_out = torch.full_like(d_in, float("nan"))
+        with gbfft.Plan(n, batch, direction, DTYPES[dtype], variant=variant) as p:
+            assert p.info()["variant"] == variant
+            p.execute(d_in, d_out)
+            torch.cuda.synchronize()
+            assert gbfft.gbfft_plan_device_status(p.handle) == 0
+        outs.append(d_out.cpu().numpy().view(np.complex64).reshape(batch, n))
+    ref = oracle.dft(x.astype(np.complex128), direction, nthreads=ncpu())
+    gate = TC_TOL_PER_LOG2N * math.log2(n)
+    err1 = row_rel_l2(outs[0], ref)
+    assert np.all(np.isfinite(err1)) and err1.max() <= gate, err1.max()
+    assert row_rel_l2(outs[0], outs[1].astype(np.complex128)).max() <= gate
