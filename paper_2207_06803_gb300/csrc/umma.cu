@@ -10,12 +10,13 @@
 //     the column as one 32-element row of the A operands Ah = Xh^T and
 //     Al = Xl^T (128 rows per MMA tile) in shared memory;
 //   - B = [Mh; Ml]^T is resident in shared memory for the whole kernel;
-//   - one elected thread issues D = Ah [Mh | Ml]^T (N = 64) and D[:, 0:32] +=
-//     Al Mh^T (N = 32), each as two K = 16 instructions, and commits them to an
-//     mbarrier; D (128 lanes x 64 FP32 columns) lives in tensor memory;
+//   - one elected thread issues D = Al Mh^T + Ah Ml^T + Ah Mh^T into the same
+//     32 TMEM columns (N = 32, each product as two K = 16 instructions) and
+//     commits them to an mbarrier; D (128 lanes x 32 FP32 columns per M tile)
+//     lives in tensor memory;
 //   - each warp reads back its own 32 TMEM lanes (its own 32 butterflies) with
-//     tcgen05.ld and forms y = D[:, 0:32] + D[:, 32:64], then writes the 16
-//     outputs with the Stockham pattern (shared-memory exchange or HBM).
+//     tcgen05.ld, then writes the 16 outputs with the Stockham pattern
+//     (shared-memory exchange or HBM).
 // Operand layout: K-major, no swizzle; a core matrix is 8 rows x 16 bytes
 // (8 halves of K), core matrices adjacent in K are 128 bytes apart (leading
 // byte offset) and 8-row groups 512 bytes apart (stride byte offset).
@@ -198,18 +199,22 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
     tc_fence_after();
     constexpr int MT = T * N / 16 / 128;
     if (tid == 0) {
-        const uint32_t idesc64 = instr_desc(PREC, 128, 64), idesc32 = instr_desc(PREC, 128, 32);
-        const uint32_t b_addr = smem_u32(sh.b);
+        const uint32_t idesc = instr_desc(PREC, 128, 32);
+        const uint32_t b_mh = smem_u32(sh.b), b_ml = b_mh + 4 * kSbo;  // rows 0-31 = Mh, 32-63 = Ml
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt) {
-            const uint32_t d = tmem + (uint32_t)(mt * 64);
+            const uint32_t d = tmem + (uint32_t)(mt * 32);
             const uint32_t ah = smem_u32(sh.a_hi + mt * kTileBytes), al = smem_u32(sh.a_lo + mt * kTileBytes);
+            // D = Al Mh^T + Ah Ml^T + Ah Mh^T (small terms first), each as two K = 16 steps
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks)  // D = Ah [Mh | Ml]^T
-                umma_f16(d, smem_desc(ah + ks * 2 * kLbo), smem_desc(b_addr + ks * 2 * kLbo), idesc64, ks);
+            for (int ks = 0; ks < 2; ++ks)
+                umma_f16(d, smem_desc(al + ks * 2 * kLbo), smem_desc(b_mh + ks * 2 * kLbo), idesc, ks);
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks)  // D[:, 0:32] += Al Mh^T
-                umma_f16(d, smem_desc(al + ks * 2 * kLbo), smem_desc(b_addr + ks * 2 * kLbo), idesc32, 1);
+            for (int ks = 0; ks < 2; ++ks)
+                umma_f16(d, smem_desc(ah + ks * 2 * kLbo), smem_desc(b_ml + ks * 2 * kLbo), idesc, 1);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks)
+                umma_f16(d, smem_desc(ah + ks * 2 * kLbo), smem_desc(b_mh + ks * 2 * kLbo), idesc, 1);
         }
         umma_commit(sh.bar);
     }
@@ -219,13 +224,12 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
     tc_fence_after();
     // Warp w reads TMEM lanes 32*(w%4) .. +31 of the D tile of its M-tile.
     const int warp = tid >> 5;
-    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
-    float d0[32], d1[32];
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 32);
+    float d0[32];
     tmem_ld32(taddr, d0);
-    tmem_ld32(taddr + 32, d1);
     float2 y[16];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) y[m] = make_float2((d0[m] + d1[m]) * inv_sc, (d0[16 + m] + d1[16 + m]) * inv_sc);
+    for (int m = 0; m < 16; ++m) y[m] = make_float2(d0[m] * inv_sc, d0[16 + m] * inv_sc);
     tc_fence_before();
     if constexpr (!FIRST && !LAST) __syncthreads();  // every column of this stage has been read from xbuf
     const int b = j / L;
@@ -259,7 +263,7 @@ __global__ void __launch_bounds__(T * N / 16) k_stockham_umma(const float2* in, 
                                                                int* status) {
     constexpr int TPB = T * N / 16;
     constexpr int MT = TPB / 128;
-    constexpr uint32_t kCols = MT == 1 ? 64 : 128;
+    constexpr uint32_t kCols = MT == 1 ? 32 : 64;
     static_assert(TPB % 128 == 0 && (MT == 1 || MT == 2), "one or two M = 128 tiles per stage");
     extern __shared__ __align__(1024) uint8_t usm[];
     UmmaShared sh;
@@ -381,8 +385,8 @@ int umma_grid(const UmmaVariant& v) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.k[0][0], v.tpb, (size_t)v.smem) != cudaSuccess)
         return 0;
-    // Each CTA holds 64 or 128 TMEM columns of the SM's 512; stay well inside.
-    const int tmem_cap = 512 / (v.tpb > 128 ? 128 : 64);
+    // Each CTA holds 32 or 64 TMEM columns of the SM's 512; stay inside.
+    const int tmem_cap = 512 / (v.tpb > 128 ? 64 : 32);
     if (per_sm > tmem_cap) per_sm = tmem_cap;
     return per_sm * sms;
 }
