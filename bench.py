@@ -65,6 +65,8 @@ def parse_args():
                     help="comma-separated subset of the sweep (for small profiling cases)")
     ap.add_argument("--dtype", type=int, default=0,
                     help="plan dtype for the sweep runner (0 FP32, 1 FP16x2 and 2 BF16x2 tensor-core; profiling)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="plan variant for the sweep runner (tensor-core dtypes: 0 mma.sync, 1 tcgen05; profiling)")
     ap.add_argument("--points-log2", type=int, default=26,
                     help="complex points per call (default 26: the 512 MiB sweep workload)")
     args = ap.parse_args()
@@ -309,7 +311,7 @@ def run_gpu(args):
     plans = []
     for n in SWEEP:
         for direction in (gbfft.GBFFT_FORWARD, gbfft.GBFFT_INVERSE):
-            plans.append(((n, direction), gbfft.Plan(n, TOTAL // n, direction, args.dtype)))
+            plans.append(((n, direction), gbfft.Plan(n, TOTAL // n, direction, args.dtype, variant=args.variant)))
     calls = len(plans)
 
     def step(events=None):
