@@ -86,10 +86,11 @@ int gbfft_version(void);
  * half-precision parts (Mh Xh + Mh Xl + Ml Xh, FP32 accumulation); FP16
  * columns are scaled by exact powers of two first.  Stage twiddles stay FP32.
  * gbfft_plan_create_variant with a tensor-core dtype selects the engine:
- * variant 0 (default) issues warp-level mma.sync.m16n8k16 on register
- * fragments; variant 1 (N = 256, 4096) issues tcgen05.mma from shared-memory
- * operands into tensor memory and reads results back with tcgen05.ld.  The
- * two-pass form is FP32-only (INVALID_ARG otherwise).
+ * variant 1 (N = 256, 4096; the default there) issues tcgen05.mma from
+ * shared-memory operands into tensor memory and reads results back with
+ * tcgen05.ld; variant 0 (the default for N = 16) issues warp-level
+ * mma.sync.m16n8k16 on register fragments.  The two-pass form is FP32-only
+ * (INVALID_ARG otherwise).
  */
 gbfft_status gbfft_plan_create(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype);
 
@@ -173,6 +174,12 @@ int gbfft_num_variants(int64_t n);
  */
 gbfft_status gbfft_variant_info(int64_t n, int index, int *nstages, int *radices, int *rows_per_cta,
                                 int *threads_per_cta, int *smem_bytes);
+
+/*
+ * Grid bound of a plan's persistent kernel (resident CTAs on the device at
+ * plan creation); 0 for one-tile-per-CTA kernels, -1 for NULL.  Diagnostic.
+ */
+int gbfft_plan_grid_cap(gbfft_plan p);
 
 /*
  * Kernel shape of variant `index` for length n: 0 one tile per CTA, 1

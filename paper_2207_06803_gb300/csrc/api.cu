@@ -229,7 +229,9 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     if (dtype != GBFFT_C2C_F32) {
         if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
         if (variant > 1) return GBFFT_ERR_NOT_FOUND;
-        return create_tc(out, n, batch, direction, dtype, variant < 0 ? 0 : variant);
+        // default engine: tcgen05 where it exists (N = 256, 4096), else mma.sync
+        const int engine = variant >= 0 ? variant : (umma_variant_for(n) ? 1 : 0);
+        return create_tc(out, n, batch, direction, dtype, engine);
     }
 
     const RowsVariant* cands[kMaxVariantsPerSize];
@@ -560,6 +562,8 @@ gbfft_status gbfft_variant_info(int64_t n, int index, int* nstages, int* radices
     if (smem_bytes) *smem_bytes = v->smem;
     return GBFFT_OK;
 }
+
+int gbfft_plan_grid_cap(gbfft_plan p) { return p ? p->grid_cap : -1; }
 
 int gbfft_variant_kind(int64_t n, int index) {
     const RowsVariant* cands[kMaxVariantsPerSize];

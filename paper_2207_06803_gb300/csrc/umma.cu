@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "internal.h"
@@ -379,16 +380,23 @@ cudaError_t prepare_umma(const UmmaVariant& v) {
     return cudaSuccess;
 }
 
+// Resident CTAs per SM from the kernel's own resources (registers, shared
+// memory, threads) and its tensor-memory columns, times the SM count.
 int umma_grid(const UmmaVariant& v) {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v.k[0][0], v.tpb, (size_t)v.smem) != cudaSuccess)
+    int dev = 0;
+    cudaDeviceProp prop;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, v.k[0][0]) != cudaSuccess)
         return 0;
-    // Each CTA holds 32 or 64 TMEM columns of the SM's 512; stay inside.
-    const int tmem_cap = 512 / (v.tpb > 128 ? 64 : 32);
-    if (per_sm > tmem_cap) per_sm = tmem_cap;
-    return per_sm * sms;
+    int per_sm = prop.maxThreadsPerMultiProcessor / v.tpb;
+    const int regs = fa.numRegs > 0 ? fa.numRegs : 255;
+    per_sm = std::min(per_sm, prop.regsPerMultiprocessor / (regs * v.tpb));
+    const int smem = v.smem + (int)fa.sharedSizeBytes + 1024;  // + per-CTA reservation
+    per_sm = std::min(per_sm, (int)prop.sharedMemPerMultiprocessor / smem);
+    per_sm = std::min(per_sm, 512 / (v.tpb > 128 ? 64 : 32));  // TMEM columns
+    per_sm = std::min(per_sm, prop.maxBlocksPerMultiProcessor);
+    return per_sm < 1 ? 0 : per_sm * prop.multiProcessorCount;
 }
 
 cudaError_t launch_umma_bmat(uint16_t* bm, int prec, int sign, cudaStream_t s) {

@@ -64,6 +64,7 @@ PROTOTYPES = {
     "gbfft_variant_info": (_c_int, [_c_i64, _c_int, _c_intp, _c_intp, _c_intp, _c_intp, _c_intp]),
     "gbfft_plan_device_status": (_c_int, [_c_vp]),
     "gbfft_variant_kind": (_c_int, [_c_i64, _c_int]),
+    "gbfft_plan_grid_cap": (_c_int, [_c_vp]),
     "gbfft_execute_twopass_noalloc": (_c_int, [_c_i64, _c_i64, _c_int, _c_vp, _c_vp, _c_vp]),
     "gbfft_plan_ragged": (_c_int, [ctypes.POINTER(_c_vp), _c_i64p, _c_i64p, _c_i64, _c_int, _c_int]),
     "gbfft_execute_ragged": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
@@ -215,6 +216,10 @@ def gbfft_variant_info(n: int, index: int) -> dict:
                                     ctypes.byref(tpb), ctypes.byref(smem)), "gbfft_variant_info")
     return {"radices": list(radices[: nst.value]), "rows_per_cta": rows.value,
             "threads_per_cta": tpb.value, "smem_bytes": smem.value}
+
+
+def gbfft_plan_grid_cap(plan: int) -> int:
+    return int(lib().gbfft_plan_grid_cap(plan))
 
 
 def gbfft_variant_kind(n: int, index: int) -> int:
