@@ -75,8 +75,15 @@ def test_tensor_core_rejects_other_sizes_and_forms():
         with pytest.raises(gbfft.GbfftError) as e:
             gbfft.gbfft_plan_create(n, 4, -1, 1)
         assert e.value.status == gbfft.GBFFT_ERR_UNSUPPORTED_SIZE
-    with pytest.raises(gbfft.GbfftError):
-        gbfft.gbfft_plan_create_variant(256, 4, -1, 1, 0)
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_create_variant(256, 4, -1, 1, 2)  # engines are 0 (mma.sync) and 1 (tcgen05)
+    assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_create_variant(16, 4, -1, 1, 1)  # no tcgen05 engine at N = 16
+    assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_create_twopass(4096, 4, -1, 1, 64)  # two-pass is FP32-only
+    assert e.value.status == gbfft.GBFFT_ERR_INVALID_ARG
 
 
 def test_bf16x2_rejected_at_n16():
