@@ -595,6 +595,8 @@ def run_ragged(args):
         res["queue_order"] = gbfft.gbfft_ragged_queue_order(rp.handle)
         res["tile_splits"] = {str(n): gbfft.gbfft_ragged_tile_split(rp.handle, int(n))
                               for n in sorted(set(sizes.tolist()))}
+        res["schedules"] = {str(n): gbfft.gbfft_ragged_schedule(rp.handle, int(n))
+                            for n in sorted(set(sizes.tolist()))}
     # (i) one launch per distinct length over a grouped copy of the data
     order = np.argsort(sizes, kind="stable")
     grouped = np.concatenate([flat[offs[i]:offs[i] + sizes[i]] for i in order])

@@ -197,6 +197,30 @@ int gbfft_variant_kind(int64_t n, int index);
 gbfft_status gbfft_plan_device_status(gbfft_plan p);
 
 /*
+ * Planner autotuner and wisdom (FFTW-style runtime planning, which the paper
+ * lists as future work).  gbfft_autotune times, on scratch device buffers of
+ * `batch` rows (allocated and freed inside the call; synchronous), every way
+ * the library can run length n in direction/dtype: each compiled single-pass
+ * variant, each two-pass split N = K*M (FP32), each tensor-core engine; it
+ * returns the fastest (*best_variant >= 0 a variant/engine index, or -1 with
+ * *best_k_outer = K for two-pass; *best_ms its median time over `reps`) and
+ * records it as wisdom.  gbfft_plan_create uses wisdom for (n, dtype,
+ * direction) when it has some.  gbfft_wisdom_export writes the table to a
+ * text file (one line per entry, tagged with the GPU name);
+ * gbfft_wisdom_import merges a file (with require_same_gpu != 0, entries from
+ * other GPU models are skipped; INVALID_ARG on a malformed file, NOT_FOUND if
+ * it cannot be opened); gbfft_wisdom_lookup queries one entry (NOT_FOUND if
+ * none); gbfft_wisdom_forget clears it.  GBFFT_WISDOM=<file> in the
+ * environment is imported once at the first plan creation.
+ */
+gbfft_status gbfft_autotune(int64_t n, int64_t batch, int direction, int dtype, int reps, int *best_variant,
+                            int64_t *best_k_outer, float *best_ms);
+gbfft_status gbfft_wisdom_lookup(int64_t n, int dtype, int direction, int *variant, int64_t *k_outer);
+gbfft_status gbfft_wisdom_export(const char *path);
+gbfft_status gbfft_wisdom_import(const char *path, int require_same_gpu);
+gbfft_status gbfft_wisdom_forget(void);
+
+/*
  * Ragged batches: `count` independent transforms of uneven lengths n[i]
  * (each of the form 2^a, 3*2^a, 5*2^a or 7*2^a within [8, 8192]; others give
  * UNSUPPORTED_SIZE), transform i occupying complex elements
@@ -221,9 +245,9 @@ gbfft_status gbfft_plan_ragged(gbfft_plan *out, const int64_t *n, const int64_t 
 gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void *cuda_stream);
 
 /*
- * Tile-shape autotuner for a ragged plan: tries both queue orders, then for
- * each length class, heaviest first, 1, 2, 4 and 8 items per full tile
- * (rows per item = T/split),
+ * Autotuner for a ragged plan: tries both queue orders, then for each length
+ * class, heaviest first, 1, 2, 4 and 8 items per full tile (rows per item =
+ * T/split), then each compiled alternative radix schedule of a length,
  * timing the whole persistent launch on `in`/`out` (median of `reps` after
  * one warm-up; `out` is overwritten) and keeps the fastest shapes.  *best_ms
  * (may be NULL) receives the best median time.  Synchronous.
@@ -234,6 +258,11 @@ gbfft_status gbfft_ragged_autotune(gbfft_plan p, const void *in, void *out, int 
  * items of one length together, heaviest length first; 0 orders all items by
  * work, heaviest first.  The autotuner tries both. */
 int gbfft_ragged_queue_order(gbfft_plan p);
+
+/* Radix schedule the plan uses for length n: its stage count (0 if n is not in
+ * the plan, -1 if not a ragged plan), radices written to `radices` (up to 8;
+ * may be NULL).  The autotuner may switch a length to an alternative schedule. */
+int gbfft_ragged_schedule(gbfft_plan p, int64_t n, int *radices);
 
 /* Number of work items in the plan's queue (-1 if not a ragged plan). */
 int64_t gbfft_ragged_num_items(gbfft_plan p);

@@ -226,6 +226,20 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
     if (dtype != GBFFT_C2C_F32 && dtype != GBFFT_C2C_F32_TC_FP16X2 && dtype != GBFFT_C2C_F32_TC_BF16X2)
         return GBFFT_ERR_INVALID_ARG;
+    if (variant < 0 && k_outer == 0) {  // no forced choice: use autotuned wisdom when there is some
+        wisdom_load_env_once();
+        int wv = -1;
+        int64_t wk = 0;
+        if (wisdom_lookup(n, dtype, direction, &wv, &wk)) {
+            if (wk > 0 && dtype == GBFFT_C2C_F32) {
+                int64_t kk, mm;
+                if (choose_split(n, wk, &kk, &mm)) k_outer = wk;
+            } else if (wv >= 0) {
+                const int limit = dtype == GBFFT_C2C_F32 ? rows_variants_for(n, nullptr, 0) : 2;
+                if (wv < limit) variant = wv;
+            }
+        }
+    }
     if (dtype != GBFFT_C2C_F32) {
         if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
         if (variant > 1) return GBFFT_ERR_NOT_FOUND;
@@ -539,6 +553,15 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds) {
 int gbfft_ragged_queue_order(gbfft_plan p) {
     if (!p || p->kind != kPlanRagged) return -1;
     return ragged_queue_order(p->ragged);
+}
+
+int gbfft_ragged_schedule(gbfft_plan p, int64_t n, int* radices) {
+    if (!p || p->kind != kPlanRagged) return -1;
+    int rad[kMaxStages];
+    const int ns = ragged_schedule(p->ragged, n, rad);
+    if (radices)
+        for (int i = 0; i < ns; ++i) radices[i] = rad[i];
+    return ns;
 }
 
 int gbfft_ragged_tile_split(gbfft_plan p, int64_t n) {

@@ -106,7 +106,13 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
                              float* best_ms);
 int ragged_class_split(const RaggedState* r, int64_t n);
 int ragged_queue_order(const RaggedState* r);
+// Radix schedule the plan uses for length n (stage count; 0 if n is absent).
+int ragged_schedule(const RaggedState* r, int64_t n, int* radix);
 bool ragged_supported(int64_t n);
+
+// Planner wisdom (autotune.cu): the autotuned choice for (n, dtype, direction).
+void wisdom_load_env_once();
+bool wisdom_lookup(int64_t n, int dtype, int direction, int* variant, int64_t* k_outer);
 
 // Per-translation-unit variant tables, gathered by the registry in api.cu.
 const RowsVariant* rows_variants_pow2(int* count);

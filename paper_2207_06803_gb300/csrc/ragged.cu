@@ -13,77 +13,6 @@
 
 namespace gbfft {
 
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-template <int S, int N, int T, int PS, int... Rs>
-__device__ __noinline__ void ragged_item(const float2* in, float2* out, const long long* s_off, float2* sm,
-                                            const float2* __restrict__ tw, int nvalid) {
-    constexpr int TPB = kRaggedThreads;
-    constexpr int E = capacity_of_r<N, T, TPB, Rs...>();
-    static_assert(T >= 1 && T <= kRaggedThreads && E <= 32, "class tile shape");
-    const IndexedIO<N> io{in, out, s_off};
-    float2 v[E];
-    gather_global<N, E, T, First<Rs...>::value, IndexedIO<N>, TPB>(v, io, nvalid);
-    run_stages_t<N, S, E, T, PS, TPB, true, 0, 1, Rs...>(v, io, sm, tw, nvalid);
-}
-
-template <int S>
-__global__ void __launch_bounds__(kRaggedThreads, 3) k_ragged(const float2* in, float2* out, const RaggedItem* items,
-                                                           int nitems, const long long* offs,
-                                                           const float2* __restrict__ tw,
-                                                           const int* __restrict__ tw_off, int* counter, int* status,
-                                                           long long wait_ns) {
-    extern __shared__ float2 sm[];
-    __shared__ long long s_off[kRaggedThreads];
-    __shared__ int s_item, s_ok;
-    for (;;) {
-        __syncthreads();  // the previous item's readers of s_off and sm are done
-        if (threadIdx.x == 0) {
-            const int it = atomicAdd(counter, 1);
-            int ok = 1;
-            if (it < nitems) {
-                const volatile int* rdy = &items[it].ready;
-                if (*rdy == 0) {
-                    const unsigned long long t0 = globaltimer_ns();
-                    while (*rdy == 0) {
-                        if (globaltimer_ns() - t0 > (unsigned long long)wait_ns) {
-                            ok = 0;
-                            atomicCAS(status, 0, (int)GBFFT_ERR_TIMEOUT);
-                            break;
-                        }
-                        __nanosleep(2000);
-                    }
-                }
-            }
-            s_item = it;
-            s_ok = ok;
-        }
-        __syncthreads();
-        const int it = s_item;
-        if (it >= nitems) break;
-        if (!s_ok) continue;
-        const RaggedItem d = items[it];
-        for (int t = threadIdx.x; t < d.count; t += kRaggedThreads) s_off[t] = offs[d.first + t];
-        __syncthreads();
-        const float2* twc = tw + tw_off[d.cls];
-        switch (d.cls) {
-#define GBFFT_RAGGED_CASE(idx, N, T, PS, ...)                                      \
-    case idx:                                                                     \
-        ragged_item<S, N, T, PS, __VA_ARGS__>(in, out, s_off, sm, twc, d.count); \
-        break;
-            GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_CASE)
-#undef GBFFT_RAGGED_CASE
-            default:
-                if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
-                break;
-        }
-    }
-}
-
 namespace {
 
 struct ClassInfo {
@@ -97,11 +26,11 @@ constexpr int count_of() {
 }
 
 #define GBFFT_RAGGED_INFO(idx, N, T, PS, ...) ClassInfo{N, T, PS, count_of<__VA_ARGS__>(), {__VA_ARGS__}},
-const ClassInfo kClasses[kRaggedClasses] = {GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_INFO)};
+const ClassInfo kClasses[kRaggedCases] = {GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_INFO)};
 #undef GBFFT_RAGGED_INFO
 
 int class_of(int64_t n) {
-    for (int c = 0; c < kRaggedClasses; ++c)
+    for (int c = 0; c < kRaggedCases; ++c)
         if (kClasses[c].n == n) return c;
     return -1;
 }
@@ -119,7 +48,7 @@ struct RaggedState {
     int64_t total = 0;  // elements spanned by the transforms (max offset + n)
     std::vector<int64_t> n, off;
     std::vector<std::vector<int64_t>> members;  // transform indices per class
-    int split[kRaggedClasses];                  // tile shape: rows per item = T_c / split[c]
+    int split[kRaggedCases];                  // tile shape: rows per item = T_c / split[c]
     int order = 1;                              // queue order: 0 = heaviest item first, 1 = grouped by class
     std::vector<RaggedItem> items;
     std::vector<long long> row_offs;
@@ -173,7 +102,7 @@ static gbfft_status ragged_build_items(RaggedState* r) {
         std::vector<long long> rows;
     };
     std::vector<Pending> pend;
-    for (int c = 0; c < kRaggedClasses; ++c) {
+    for (int c = 0; c < kRaggedCases; ++c) {
         const std::vector<int64_t>& mem = r->members[c];
         if (mem.empty()) continue;
         int rows = kClasses[c].t / r->split[c];
@@ -190,7 +119,7 @@ static gbfft_status ragged_build_items(RaggedState* r) {
     if (r->order == 0) {
         std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
     } else {
-        std::vector<double> cls_cost(kRaggedClasses, 0.0);
+        std::vector<double> cls_cost(kRaggedCases, 0.0);
         for (const Pending& p : pend) cls_cost[p.cls] = std::max(cls_cost[p.cls], p.cost);
         std::stable_sort(pend.begin(), pend.end(), [&](const Pending& a, const Pending& b) {
             if (a.cls != b.cls) return cls_cost[a.cls] > cls_cost[b.cls] || (cls_cost[a.cls] == cls_cost[b.cls] && a.cls > b.cls);
@@ -232,7 +161,7 @@ static cudaError_t ragged_launch(RaggedState* r, int direction, const void* in, 
     float2* pout = (float2*)out;
     void* args[] = {(void*)&pin, (void*)&pout, (void*)&r->d_items, (void*)&nitems, (void*)&r->d_offs,
                     (void*)&r->d_tw,  (void*)&r->d_twoff, (void*)&r->d_counter, (void*)&status, (void*)&r->wait_ns};
-    const void* fn = direction == GBFFT_FORWARD ? (const void*)&k_ragged<-1> : (const void*)&k_ragged<+1>;
+    const void* fn = direction == GBFFT_FORWARD ? ragged_kernel_fwd() : ragged_kernel_inv();
     int grid = std::min<int>(r->grid, nitems > 0 ? nitems : 1);
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRaggedThreads), args, (size_t)r->smem, s);
 }
@@ -245,8 +174,8 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
     r->count = count;
     r->n.assign(n, n + count);
     r->off.assign(offsets, offsets + count);
-    r->members.assign(kRaggedClasses, {});
-    for (int c = 0; c < kRaggedClasses; ++c) r->split[c] = 1;
+    r->members.assign(kRaggedCases, {});
+    for (int c = 0; c < kRaggedCases; ++c) r->split[c] = 1;
     std::vector<std::pair<int64_t, int64_t>> spans;
     spans.reserve(count);
     for (int64_t i = 0; i < count; ++i) {
@@ -270,34 +199,39 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
             return GBFFT_ERR_OVERLAP;
         }
     }
-    // Stage-twiddle blocks of every class present, concatenated.
-    std::vector<int> twoff(kRaggedClasses, 0);
+    // Stage-twiddle blocks of every compiled case whose length is present
+    // (default and alternative schedules), concatenated.
+    std::vector<char> present(kRaggedCases, 0);
+    for (int c = 0; c < kRaggedCases; ++c)
+        for (int d = 0; d < kRaggedCases; ++d)
+            if (!r->members[d].empty() && kClasses[d].n == kClasses[c].n) present[c] = 1;
+    std::vector<int> twoff(kRaggedCases, 0);
     int tw_total = 0;
     r->smem = 0;
-    for (int c = 0; c < kRaggedClasses; ++c) {
-        if (r->members[c].empty()) continue;
+    for (int c = 0; c < kRaggedCases; ++c) {
+        if (!present[c]) continue;
         twoff[c] = tw_total;
         tw_total += stage_twiddle_count(kClasses[c].radix, kClasses[c].nstages);
         r->smem = std::max(r->smem, class_smem_bytes(c));
     }
     gbfft_status st = GBFFT_OK;
     if (cudaMalloc(&r->d_tw, sizeof(float2) * (size_t)std::max(tw_total, 1)) != cudaSuccess ||
-        cudaMalloc(&r->d_twoff, sizeof(int) * kRaggedClasses) != cudaSuccess ||
+        cudaMalloc(&r->d_twoff, sizeof(int) * kRaggedCases) != cudaSuccess ||
         cudaMalloc(&r->d_counter, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         st = GBFFT_ERR_OOM;
     }
-    for (int c = 0; st == GBFFT_OK && c < kRaggedClasses; ++c) {
-        if (r->members[c].empty()) continue;
+    for (int c = 0; st == GBFFT_OK && c < kRaggedCases; ++c) {
+        if (!present[c]) continue;
         if (launch_stage_twiddles(r->d_tw + twoff[c], kClasses[c].n, kClasses[c].radix, kClasses[c].nstages, 0) !=
             cudaSuccess)
             st = GBFFT_ERR_CUDA;
     }
     if (st == GBFFT_OK &&
-        cudaMemcpy(r->d_twoff, twoff.data(), sizeof(int) * kRaggedClasses, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(r->d_twoff, twoff.data(), sizeof(int) * kRaggedCases, cudaMemcpyHostToDevice) != cudaSuccess)
         st = GBFFT_ERR_CUDA;
     if (st == GBFFT_OK) {
-        const void* ks[2] = {(const void*)&k_ragged<-1>, (const void*)&k_ragged<+1>};
+        const void* ks[2] = {ragged_kernel_fwd(), ragged_kernel_inv()};
         int dev = 0, sms = 0, per_sm = 0;
         for (const void* k : ks)
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem) != cudaSuccess)
@@ -399,10 +333,11 @@ void ragged_set_wait_ns(RaggedState* r, long long ns) {
     ragged_release_graph(r);  // the limit is a kernel argument baked into the graph
 }
 
-// Tile-shape autotuner: coordinate descent over the rows-per-item split of each
-// class (1, 2, 4, 8), heaviest classes first, timing the whole direct launch
-// with CUDA events (median of `reps`).  Keeps the best shapes and rebuilds the
-// queue; the graph is re-captured on the next execute.
+// Autotuner: queue order, then coordinate descent over the rows-per-item
+// split of each class (1, 2, 4, 8), heaviest classes first, then each
+// length's compiled alternative radix schedules, timing the whole direct
+// launch with CUDA events (median of `reps`).  Keeps the best choices and
+// rebuilds the queue; the graph is re-captured on the next execute.
 gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void* out, int* status, int reps,
                              float* best_ms) {
     cudaStream_t s;
@@ -439,7 +374,7 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
         else r->order = keep;
     }
     std::vector<int> order;
-    for (int c = 0; c < kRaggedClasses; ++c)
+    for (int c = 0; c < kRaggedCases; ++c)
         if (!r->members[c].empty()) order.push_back(c);
     std::sort(order.begin(), order.end(), [&](int a, int b) {
         return (double)r->members[a].size() * kClasses[a].n > (double)r->members[b].size() * kClasses[b].n;
@@ -461,6 +396,28 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
         }
         r->split[c] = best_split;
     }
+    // Radix schedule per length: move a length's transforms to each compiled
+    // alternative case and keep the fastest.
+    std::vector<int64_t> tuned;
+    for (int c = 0; st == GBFFT_OK && c < kRaggedCases; ++c) {
+        if (r->members[c].empty()) continue;
+        if (std::find(tuned.begin(), tuned.end(), kClasses[c].n) != tuned.end()) continue;
+        tuned.push_back(kClasses[c].n);
+        int cur = c;
+        for (int a = 0; a < kRaggedCases && st == GBFFT_OK; ++a) {
+            if (a == cur || kClasses[a].n != kClasses[c].n || !r->members[a].empty()) continue;
+            r->members[a].swap(r->members[cur]);
+            if (kClasses[a].t == kClasses[cur].t) r->split[a] = r->split[cur];  // same tile shape
+            float ms = 0.f;
+            st = measure(&ms);
+            if (st == GBFFT_OK && ms < best) {
+                best = ms;
+                cur = a;
+            } else {
+                r->members[cur].swap(r->members[a]);
+            }
+        }
+    }
     if (st == GBFFT_OK) st = ragged_build_items(r);
     ragged_release_graph(r);
     cudaEventDestroy(e0);
@@ -473,9 +430,23 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
 
 int ragged_queue_order(const RaggedState* r) { return r->order; }
 
+// The case currently used for length n (the one holding its transforms).
+static int case_in_use(const RaggedState* r, int64_t n) {
+    for (int c = 0; c < kRaggedCases; ++c)
+        if (kClasses[c].n == n && !r->members[c].empty()) return c;
+    return -1;
+}
+
 int ragged_class_split(const RaggedState* r, int64_t n) {
-    const int c = class_of(n);
+    const int c = case_in_use(r, n);
     return c < 0 ? 0 : r->split[c];
+}
+
+int ragged_schedule(const RaggedState* r, int64_t n, int* radix) {
+    const int c = case_in_use(r, n);
+    if (c < 0) return 0;
+    for (int i = 0; i < kClasses[c].nstages; ++i) radix[i] = kClasses[c].radix[i];
+    return kClasses[c].nstages;
 }
 
 bool ragged_supported(int64_t n) { return class_of(n) >= 0; }

@@ -1,0 +1,13 @@
+// Forward-direction instantiation of the ragged persistent kernel (compiled
+// apart from the inverse so the two build in parallel).
+#include "internal.h"
+#include "ragged.cuh"
+
+namespace gbfft {
+
+template __global__ void k_ragged<-1>(const float2*, float2*, const RaggedItem*, int, const long long*,
+                                      const float2* __restrict__, const int* __restrict__, int*, int*, long long);
+
+const void* ragged_kernel_fwd() { return (const void*)&k_ragged<-1>; }
+
+}  // namespace gbfft

@@ -65,6 +65,12 @@ PROTOTYPES = {
     "gbfft_plan_device_status": (_c_int, [_c_vp]),
     "gbfft_variant_kind": (_c_int, [_c_i64, _c_int]),
     "gbfft_plan_grid_cap": (_c_int, [_c_vp]),
+    "gbfft_autotune": (_c_int, [_c_i64, _c_i64, _c_int, _c_int, _c_int, _c_intp, _c_i64p,
+                                ctypes.POINTER(ctypes.c_float)]),
+    "gbfft_wisdom_lookup": (_c_int, [_c_i64, _c_int, _c_int, _c_intp, _c_i64p]),
+    "gbfft_wisdom_export": (_c_int, [ctypes.c_char_p]),
+    "gbfft_wisdom_import": (_c_int, [ctypes.c_char_p, _c_int]),
+    "gbfft_wisdom_forget": (_c_int, []),
     "gbfft_execute_twopass_noalloc": (_c_int, [_c_i64, _c_i64, _c_int, _c_vp, _c_vp, _c_vp]),
     "gbfft_plan_ragged": (_c_int, [ctypes.POINTER(_c_vp), _c_i64p, _c_i64p, _c_i64, _c_int, _c_int]),
     "gbfft_execute_ragged": (_c_int, [_c_vp, _c_vp, _c_vp, _c_vp]),
@@ -72,6 +78,7 @@ PROTOTYPES = {
     "gbfft_ragged_num_items": (_c_i64, [_c_vp]),
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
     "gbfft_ragged_queue_order": (_c_int, [_c_vp]),
+    "gbfft_ragged_schedule": (_c_int, [_c_vp, _c_i64, _c_intp]),
     "gbfft_ragged_set_item_ready": (_c_int, [_c_vp, _c_i64, _c_int]),
     "gbfft_ragged_set_wait_limit": (_c_int, [_c_vp, _c_i64]),
     "gbfft_server_create": (_c_int, [ctypes.POINTER(_c_vp), _c_size, _c_int, _c_int]),
@@ -218,6 +225,36 @@ def gbfft_variant_info(n: int, index: int) -> dict:
             "threads_per_cta": tpb.value, "smem_bytes": smem.value}
 
 
+def gbfft_autotune(n: int, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32,
+                   reps: int = 5) -> dict:
+    v, k, ms = ctypes.c_int(), ctypes.c_int64(), ctypes.c_float()
+    _check(lib().gbfft_autotune(n, batch, direction, dtype, reps, ctypes.byref(v), ctypes.byref(k), ctypes.byref(ms)),
+           "gbfft_autotune")
+    return {"variant": v.value, "k_outer": k.value, "ms": ms.value}
+
+
+def gbfft_wisdom_lookup(n: int, dtype: int = GBFFT_C2C_F32, direction: int = GBFFT_FORWARD):
+    """(variant, k_outer) recorded for (n, dtype, direction), or None."""
+    v, k = ctypes.c_int(), ctypes.c_int64()
+    rc = lib().gbfft_wisdom_lookup(n, dtype, direction, ctypes.byref(v), ctypes.byref(k))
+    if rc == GBFFT_ERR_NOT_FOUND:
+        return None
+    _check(rc, "gbfft_wisdom_lookup")
+    return v.value, k.value
+
+
+def gbfft_wisdom_export(path: str) -> None:
+    _check(lib().gbfft_wisdom_export(os.fsencode(path)), "gbfft_wisdom_export")
+
+
+def gbfft_wisdom_import(path: str, require_same_gpu: bool = True) -> None:
+    _check(lib().gbfft_wisdom_import(os.fsencode(path), 1 if require_same_gpu else 0), "gbfft_wisdom_import")
+
+
+def gbfft_wisdom_forget() -> None:
+    _check(lib().gbfft_wisdom_forget(), "gbfft_wisdom_forget")
+
+
 def gbfft_plan_grid_cap(plan: int) -> int:
     return int(lib().gbfft_plan_grid_cap(plan))
 
@@ -264,6 +301,12 @@ def gbfft_ragged_num_items(plan: int) -> int:
 
 def gbfft_ragged_tile_split(plan: int, n: int) -> int:
     return int(lib().gbfft_ragged_tile_split(plan, n))
+
+
+def gbfft_ragged_schedule(plan: int, n: int) -> list[int]:
+    rad = (ctypes.c_int * 8)()
+    ns = int(lib().gbfft_ragged_schedule(plan, n, rad))
+    return list(rad[:max(ns, 0)])
 
 
 def gbfft_ragged_queue_order(plan: int) -> int:

@@ -91,6 +91,9 @@ def test_autotuned_shapes_give_identical_results():
         assert ms > 0
         splits = {n: gbfft.gbfft_ragged_tile_split(p.handle, n) for n in set(sizes.tolist())}
         assert set(splits.values()) <= {1, 2, 4, 8}
+        for n in set(sizes.tolist()):
+            rad = gbfft.gbfft_ragged_schedule(p.handle, n)
+            assert rad and int(np.prod(rad)) == n
         d_out.fill_(float("nan"))
         p.execute(d_in, d_out)
         torch.cuda.synchronize()

@@ -186,3 +186,28 @@ def test_full_size_sweep_sampled_rows(direction):
         y = d_out.view(batch, 2 * n).index_select(0, idx).cpu().numpy().view(np.complex64)
         x = flat.reshape(batch, n)[rows]
         check(y, x, direction)
+
+
+def test_autotune_records_wisdom_that_plans_use(tmp_path):
+    from paper_2207_06803_gb300 import gbfft
+    gbfft.gbfft_wisdom_forget()
+    try:
+        for n in (1024, 4096, 8192):
+            best = gbfft.gbfft_autotune(n, (1 << 22) // n, -1, 0, reps=3)
+            assert best["ms"] > 0
+            assert gbfft.gbfft_wisdom_lookup(n, 0, -1) == (best["variant"], best["k_outer"])
+            with gbfft.Plan(n, 8, -1) as p:
+                info = p.info()
+                if best["k_outer"] > 0:
+                    assert info["k_outer"] == best["k_outer"]
+                else:
+                    assert info["variant"] == best["variant"]
+        path = tmp_path / "wisdom.txt"
+        gbfft.gbfft_wisdom_export(str(path))
+        gbfft.gbfft_wisdom_forget()
+        gbfft.gbfft_wisdom_import(str(path), require_same_gpu=True)
+        assert gbfft.gbfft_wisdom_lookup(4096, 0, -1) is not None
+        x = synth.uniform_batch(SEED, 4096, 9)
+        check(gpu_fft(x, -1), x, -1)  # a wisdom-driven plan still matches the oracle
+    finally:
+        gbfft.gbfft_wisdom_forget()
