@@ -67,6 +67,8 @@ def parse_args():
                     help="plan dtype for the sweep runner (0 FP32, 1 FP16x2 and 2 BF16x2 tensor-core; profiling)")
     ap.add_argument("--variant", type=int, default=None,
                     help="plan variant for the sweep runner (tensor-core dtypes: 0 mma.sync, 1 tcgen05; profiling)")
+    ap.add_argument("--ragged-graph-only", action="store_true",
+                    help="ragged config: time only the single persistent launch (for profiling)")
     ap.add_argument("--points-log2", type=int, default=26,
                     help="complex points per call (default 26: the 512 MiB sweep workload)")
     args = ap.parse_args()
@@ -597,6 +599,8 @@ def run_ragged(args):
                               for n in sorted(set(sizes.tolist()))}
         res["schedules"] = {str(n): gbfft.gbfft_ragged_schedule(rp.handle, int(n))
                             for n in sorted(set(sizes.tolist()))}
+    if args.ragged_graph_only:
+        return {"config": "ragged", "metric": "ragged batch GB/s on sum(16*N_i)", "unit": "GB/s", "results": res}
     # (i) one launch per distinct length over a grouped copy of the data
     order = np.argsort(sizes, kind="stable")
     grouped = np.concatenate([flat[offs[i]:offs[i] + sizes[i]] for i in order])

@@ -222,13 +222,15 @@ gbfft_status gbfft_wisdom_forget(void);
 
 /*
  * Ragged batches: `count` independent transforms of uneven lengths n[i]
- * (each of the form 2^a, 3*2^a, 5*2^a or 7*2^a within [8, 8192]; others give
+ * (any 1 <= n[i] <= 8192 whose prime factors are 2, 3, 5 and 7; others give
  * UNSUPPORTED_SIZE), transform i occupying complex elements
  * [offsets[i], offsets[i] + n[i]) of both the input and the output buffer
  * (typically packed back to back).  Transforms must not overlap each other
  * (OVERLAP).  Each is DFT_{n[i]} of Sec. II in direction `direction`.  The
- * plan groups the transforms by length, cuts each group into work items of a
- * tile shape (rows per item) and uploads an item queue ordered longest-first;
+ * plan groups the transforms by length, gives each length a Stockham radix
+ * schedule over the radices 2, 3, 4, 5, 7, 8, 16 (read by the kernel at run
+ * time), cuts each group into work items of a tile shape (rows per item, at
+ * most 8192 elements and 512 rows) and uploads an item queue;
  * gbfft_execute_ragged then runs ONE persistent kernel launch in which every
  * CTA claims items from the queue until it is empty, replayed from a CUDA
  * graph (the counter reset and the launch, captured on the first execute and
@@ -245,12 +247,13 @@ gbfft_status gbfft_plan_ragged(gbfft_plan *out, const int64_t *n, const int64_t 
 gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void *cuda_stream);
 
 /*
- * Autotuner for a ragged plan: tries both queue orders, then for each length
- * class, heaviest first, 1, 2, 4 and 8 items per full tile (rows per item =
- * T/split), then each compiled alternative radix schedule of a length,
- * timing the whole persistent launch on `in`/`out` (median of `reps` after
- * one warm-up; `out` is overwritten) and keeps the fastest shapes.  *best_ms
- * (may be NULL) receives the best median time.  Synchronous.
+ * Autotuner for a ragged plan: tries both queue orders, then for each length,
+ * heaviest first, the tile split 1, 2, 4, 8 (rows per item = (8192/n)/split,
+ * at most 512), each candidate radix schedule of the length and the shared
+ * memory padding, timing the whole persistent launch on `in`/`out` (median of
+ * `reps` after one warm-up; `out` is overwritten), keeping each change that
+ * makes it faster.  *best_ms (may be NULL) receives the best median time.
+ * Synchronous.
  */
 gbfft_status gbfft_ragged_autotune(gbfft_plan p, const void *in, void *out, int reps, float *best_ms);
 
@@ -267,8 +270,8 @@ int gbfft_ragged_schedule(gbfft_plan p, int64_t n, int *radices);
 /* Number of work items in the plan's queue (-1 if not a ragged plan). */
 int64_t gbfft_ragged_num_items(gbfft_plan p);
 
-/* The autotuned split of the tile shape for length n (rows per item =
- * T_n / split), 0 if n has no class in this plan. */
+/* The tile split the plan uses for length n (rows per item =
+ * (8192/n)/split, at most 512), 0 if n is not in this plan. */
 int gbfft_ragged_tile_split(gbfft_plan p, int64_t n);
 
 /*

@@ -1,5 +1,5 @@
-// Ragged-batch plans: the persistent kernel of ragged.cuh, its work queue,
-// the CUDA graph that launches it, and the tile-shape autotuner.
+// Ragged-batch plans: the persistent kernel of ragged.cuh, its work queue and
+// per-length schedules, the CUDA graph that launches it, and the autotuner.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -15,49 +15,86 @@ namespace gbfft {
 
 namespace {
 
-struct ClassInfo {
-    int n, t, ps, nstages;
-    int radix[kMaxStages];
-};
-
-template <int... Rs>
-constexpr int count_of() {
-    return (int)sizeof...(Rs);
+// Candidate radix schedules of a length n = 2^a 3^b 5^c 7^d <= 8192, the
+// default first: odd radices first, then the power-of-two part as radix-16
+// stages with the remainder first or last, or as radix-8 stages; powers of two
+// up to 16 use two stages so that both HBM passes are coalesced.  Empty if n
+// has another prime factor.
+std::vector<std::vector<int>> schedules_of(int64_t n) {
+    std::vector<std::vector<int>> out;
+    if (n < 1 || n > kRaggedMaxN) return out;
+    std::vector<int> odd;
+    int64_t m = n;
+    for (int p : {3, 5, 7})
+        while (m % p == 0) {
+            odd.push_back(p);
+            m /= p;
+        }
+    int a = 0;
+    while (m % 2 == 0) {
+        ++a;
+        m /= 2;
+    }
+    if (m != 1) return out;
+    auto add = [&](std::vector<int> pw, bool front) {
+        std::vector<int> sch = odd;
+        sch.insert(sch.end(), pw.begin(), pw.end());
+        if ((int)sch.size() > kRaggedMaxStages) return;
+        for (const auto& c : out)
+            if (c == sch) return;
+        if (front) out.insert(out.begin(), sch);
+        else out.push_back(sch);
+    };
+    auto pieces = [](int a, int unit, bool rem_first) {
+        std::vector<int> v;
+        const int full = a / unit, rem = a % unit;
+        if (rem && rem_first) v.push_back(1 << rem);
+        for (int i = 0; i < full; ++i) v.push_back(1 << unit);
+        if (rem && !rem_first) v.push_back(1 << rem);
+        return v;
+    };
+    add(pieces(a, 4, true), false);
+    add(pieces(a, 4, false), false);
+    add(pieces(a, 3, false), false);
+    add(pieces(a, 3, true), false);
+    if (odd.empty() && a == 3) add({2, 4}, true);
+    if (odd.empty() && a == 4) add({4, 4}, true);
+    return out;
 }
 
-#define GBFFT_RAGGED_INFO(idx, N, T, PS, ...) ClassInfo{N, T, PS, count_of<__VA_ARGS__>(), {__VA_ARGS__}},
-const ClassInfo kClasses[kRaggedCases] = {GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_INFO)};
-#undef GBFFT_RAGGED_INFO
-
-int class_of(int64_t n) {
-    for (int c = 0; c < kRaggedCases; ++c)
-        if (kClasses[c].n == n) return c;
-    return -1;
-}
-
-int class_smem_bytes(int c) {
-    const ClassInfo& k = kClasses[c];
-    const int elems = k.t * k.n;
-    return (int)sizeof(float2) * ((elems - 1) + ((elems - 1) >> k.ps) + 1);
+// Default shared-memory pad shift: one slot per 16 for lengths whose odd part
+// is 1 or 3 (their exchanges stride by powers of two), none otherwise.
+int default_pad(int64_t n) {
+    int64_t m = n;
+    while (m % 2 == 0) m /= 2;
+    return (m == 1 || m == 3) ? 4 : kRaggedNoPad;
 }
 
 }  // namespace
+
+struct RaggedLenState {
+    int64_t n = 0;
+    std::vector<int64_t> members;               // transform indices of this length
+    std::vector<std::vector<int>> cands;        // candidate schedules
+    std::vector<int> tw_base;                   // twiddle-table offset of each candidate
+    int cand = 0;                               // schedule in use
+    int split = 1;                              // tile shape: rows per item = (8192 / n) / split
+    int ps = kRaggedNoPad;                      // shared-memory pad shift
+};
 
 struct RaggedState {
     int64_t count = 0;
     int64_t total = 0;  // elements spanned by the transforms (max offset + n)
     std::vector<int64_t> n, off;
-    std::vector<std::vector<int64_t>> members;  // transform indices per class
-    int split[kRaggedCases];                  // tile shape: rows per item = T_c / split[c]
-    int order = 1;                              // queue order: 0 = heaviest item first, 1 = grouped by class
+    std::vector<RaggedLenState> lens;           // one per distinct length
+    int order = 1;                              // queue order: 0 = heaviest item first, 1 = grouped by length
     std::vector<RaggedItem> items;
     std::vector<long long> row_offs;
     RaggedItem* d_items = nullptr;
     long long* d_offs = nullptr;
+    RaggedLen* d_lens = nullptr;
     float2* d_tw = nullptr;
-    int* d_twoff = nullptr;
     int* d_counter = nullptr;
-    int smem = 0;
     int grid = 0;
     long long wait_ns = 200000000LL;  // 200 ms bound on any ready-wait
     cudaGraph_t graph = nullptr;
@@ -80,19 +117,46 @@ void ragged_destroy(RaggedState* r) {
     ragged_release_graph(r);
     if (r->d_items) cudaFree(r->d_items);
     if (r->d_offs) cudaFree(r->d_offs);
+    if (r->d_lens) cudaFree(r->d_lens);
     if (r->d_tw) cudaFree(r->d_tw);
-    if (r->d_twoff) cudaFree(r->d_twoff);
     if (r->d_counter) cudaFree(r->d_counter);
     delete r;
 }
 
-// Items from the current tile shapes: class groups cut into items of
-// ceil(T_c / split_c) rows.  Order 0: all items by work (rows * N log N),
+static int rows_per_item(const RaggedLenState& L) {
+    const int64_t rows = (int64_t)kRaggedTile / L.n / L.split;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kRaggedMaxRows, rows));
+}
+
+// Device descriptor of a length from its current schedule and pad.
+static RaggedLen describe(const RaggedLenState& L) {
+    RaggedLen d{};
+    const std::vector<int>& sch = L.cands[L.cand];
+    d.n = (int)L.n;
+    d.nstages = (int)sch.size();
+    d.ps = L.ps;
+    d.rcp_n = 1.0f / (float)L.n;
+    int l = 1, tw = L.tw_base[L.cand];
+    for (int s = 0; s < d.nstages; ++s) {
+        RaggedStage& st = d.st[s];
+        st.r = sch[s];
+        st.l = l;
+        st.nr = (int)L.n / sch[s];
+        st.tw = tw;
+        st.rcp_nr = 1.0f / (float)st.nr;
+        st.rcp_l = 1.0f / (float)l;
+        if (l > 1) tw += (sch[s] - 1) * l;
+        l *= sch[s];
+    }
+    return d;
+}
+
+// Items from the current tile shapes: each length's transforms cut into items
+// of rows_per_item rows.  Order 0: all items by work (rows * n log n),
 // heaviest first (longest-processing-time list scheduling).  Order 1: items
-// stay grouped by class, classes ordered by item work, heaviest first, so
-// that CTAs claiming neighbouring items run the same class's code (the
-// kernel holds one fully unrolled schedule per class; interleaving classes
-// thrashes the instruction cache).
+// stay grouped by length, lengths ordered by item work, heaviest first, so
+// that CTAs claiming neighbouring items run the same schedule.  Also uploads
+// the length descriptors.
 static gbfft_status ragged_build_items(RaggedState* r) {
     r->items.clear();
     r->row_offs.clear();
@@ -102,27 +166,27 @@ static gbfft_status ragged_build_items(RaggedState* r) {
         std::vector<long long> rows;
     };
     std::vector<Pending> pend;
-    for (int c = 0; c < kRaggedCases; ++c) {
-        const std::vector<int64_t>& mem = r->members[c];
-        if (mem.empty()) continue;
-        int rows = kClasses[c].t / r->split[c];
-        if (rows < 1) rows = 1;
-        for (size_t i = 0; i < mem.size(); i += rows) {
+    const int nl = (int)r->lens.size();
+    for (int c = 0; c < nl; ++c) {
+        const RaggedLenState& L = r->lens[c];
+        const int rows = rows_per_item(L);
+        for (size_t i = 0; i < L.members.size(); i += rows) {
             Pending p;
             p.cls = c;
-            const size_t e = std::min(mem.size(), i + (size_t)rows);
-            for (size_t k = i; k < e; ++k) p.rows.push_back((long long)r->off[mem[k]]);
-            p.cost = (double)p.rows.size() * kClasses[c].n * std::log2((double)kClasses[c].n);
+            const size_t e = std::min(L.members.size(), i + (size_t)rows);
+            for (size_t k = i; k < e; ++k) p.rows.push_back((long long)r->off[L.members[k]]);
+            p.cost = (double)p.rows.size() * L.n * std::max(1.0, std::log2((double)L.n));
             pend.push_back(std::move(p));
         }
     }
     if (r->order == 0) {
         std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
     } else {
-        std::vector<double> cls_cost(kRaggedCases, 0.0);
+        std::vector<double> cls_cost(nl, 0.0);
         for (const Pending& p : pend) cls_cost[p.cls] = std::max(cls_cost[p.cls], p.cost);
         std::stable_sort(pend.begin(), pend.end(), [&](const Pending& a, const Pending& b) {
-            if (a.cls != b.cls) return cls_cost[a.cls] > cls_cost[b.cls] || (cls_cost[a.cls] == cls_cost[b.cls] && a.cls > b.cls);
+            if (a.cls != b.cls)
+                return cls_cost[a.cls] > cls_cost[b.cls] || (cls_cost[a.cls] == cls_cost[b.cls] && a.cls > b.cls);
             return a.cost > b.cost;
         });
     }
@@ -135,6 +199,8 @@ static gbfft_status ragged_build_items(RaggedState* r) {
         r->items.push_back(it);
         r->row_offs.insert(r->row_offs.end(), p.rows.begin(), p.rows.end());
     }
+    std::vector<RaggedLen> desc(nl);
+    for (int c = 0; c < nl; ++c) desc[c] = describe(r->lens[c]);
     if (r->d_items) cudaFree(r->d_items);
     if (r->d_offs) cudaFree(r->d_offs);
     r->d_items = nullptr;
@@ -147,9 +213,23 @@ static gbfft_status ragged_build_items(RaggedState* r) {
     if (cudaMemcpy(r->d_items, r->items.data(), sizeof(RaggedItem) * r->items.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(r->d_offs, r->row_offs.data(), sizeof(long long) * r->row_offs.size(),
-                   cudaMemcpyHostToDevice) != cudaSuccess)
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(r->d_lens, desc.data(), sizeof(RaggedLen) * nl, cudaMemcpyHostToDevice) != cudaSuccess)
         return GBFFT_ERR_CUDA;
     return GBFFT_OK;
+}
+
+static void ragged_args(RaggedState* r, const float2** pin, float2** pout, int* nitems, int** status, void** args) {
+    args[0] = (void*)pin;
+    args[1] = (void*)pout;
+    args[2] = (void*)&r->d_items;
+    args[3] = (void*)nitems;
+    args[4] = (void*)&r->d_offs;
+    args[5] = (void*)&r->d_lens;
+    args[6] = (void*)&r->d_tw;
+    args[7] = (void*)&r->d_counter;
+    args[8] = (void*)status;
+    args[9] = (void*)&r->wait_ns;
 }
 
 static cudaError_t ragged_launch(RaggedState* r, int direction, const void* in, void* out, int* status,
@@ -159,11 +239,11 @@ static cudaError_t ragged_launch(RaggedState* r, int direction, const void* in, 
     int nitems = (int)r->items.size();
     const float2* pin = (const float2*)in;
     float2* pout = (float2*)out;
-    void* args[] = {(void*)&pin, (void*)&pout, (void*)&r->d_items, (void*)&nitems, (void*)&r->d_offs,
-                    (void*)&r->d_tw,  (void*)&r->d_twoff, (void*)&r->d_counter, (void*)&status, (void*)&r->wait_ns};
+    void* args[10];
+    ragged_args(r, &pin, &pout, &nitems, &status, args);
     const void* fn = direction == GBFFT_FORWARD ? ragged_kernel_fwd() : ragged_kernel_inv();
-    int grid = std::min<int>(r->grid, nitems > 0 ? nitems : 1);
-    return cudaLaunchKernel(fn, dim3(grid), dim3(kRaggedThreads), args, (size_t)r->smem, s);
+    const int grid = std::min<int>(r->grid, nitems > 0 ? nitems : 1);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kRaggedThreads), args, (size_t)kRaggedSmemBytes, s);
 }
 
 gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* offsets, int64_t count) {
@@ -174,23 +254,25 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
     r->count = count;
     r->n.assign(n, n + count);
     r->off.assign(offsets, offsets + count);
-    r->members.assign(kRaggedCases, {});
-    for (int c = 0; c < kRaggedCases; ++c) r->split[c] = 1;
     std::vector<std::pair<int64_t, int64_t>> spans;
     spans.reserve(count);
+    std::vector<int64_t> distinct;
     for (int64_t i = 0; i < count; ++i) {
         if (n[i] < 1 || offsets[i] < 0) {
             delete r;
             return GBFFT_ERR_INVALID_ARG;
         }
-        const int c = class_of(n[i]);
-        if (c < 0) {
+        if (!ragged_supported(n[i])) {
             delete r;
             return GBFFT_ERR_UNSUPPORTED_SIZE;
         }
-        r->members[c].push_back(i);
+        distinct.push_back(n[i]);
         spans.push_back({offsets[i], offsets[i] + n[i]});
         r->total = std::max(r->total, offsets[i] + n[i]);
+    }
+    if (r->total > ((int64_t)1 << 40)) {
+        delete r;
+        return GBFFT_ERR_INVALID_ARG;
     }
     std::sort(spans.begin(), spans.end());
     for (size_t i = 1; i < spans.size(); ++i) {
@@ -199,48 +281,51 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
             return GBFFT_ERR_OVERLAP;
         }
     }
-    // Stage-twiddle blocks of every compiled case whose length is present
-    // (default and alternative schedules), concatenated.
-    std::vector<char> present(kRaggedCases, 0);
-    for (int c = 0; c < kRaggedCases; ++c)
-        for (int d = 0; d < kRaggedCases; ++d)
-            if (!r->members[d].empty() && kClasses[d].n == kClasses[c].n) present[c] = 1;
-    std::vector<int> twoff(kRaggedCases, 0);
+    std::sort(distinct.begin(), distinct.end());
+    distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+    r->lens.resize(distinct.size());
     int tw_total = 0;
-    r->smem = 0;
-    for (int c = 0; c < kRaggedCases; ++c) {
-        if (!present[c]) continue;
-        twoff[c] = tw_total;
-        tw_total += stage_twiddle_count(kClasses[c].radix, kClasses[c].nstages);
-        r->smem = std::max(r->smem, class_smem_bytes(c));
+    for (size_t c = 0; c < distinct.size(); ++c) {
+        RaggedLenState& L = r->lens[c];
+        L.n = distinct[c];
+        L.cands = schedules_of(L.n);
+        L.ps = default_pad(L.n);
+        for (const auto& sch : L.cands) {
+            L.tw_base.push_back(tw_total);
+            tw_total += stage_twiddle_count(sch.data(), (int)sch.size());
+        }
     }
+    for (int64_t i = 0; i < count; ++i) {
+        const size_t c = std::lower_bound(distinct.begin(), distinct.end(), n[i]) - distinct.begin();
+        r->lens[c].members.push_back(i);
+    }
+    // Stage-twiddle blocks of every candidate schedule of every length, concatenated.
     gbfft_status st = GBFFT_OK;
     if (cudaMalloc(&r->d_tw, sizeof(float2) * (size_t)std::max(tw_total, 1)) != cudaSuccess ||
-        cudaMalloc(&r->d_twoff, sizeof(int) * kRaggedCases) != cudaSuccess ||
+        cudaMalloc(&r->d_lens, sizeof(RaggedLen) * r->lens.size()) != cudaSuccess ||
         cudaMalloc(&r->d_counter, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         st = GBFFT_ERR_OOM;
     }
-    for (int c = 0; st == GBFFT_OK && c < kRaggedCases; ++c) {
-        if (!present[c]) continue;
-        if (launch_stage_twiddles(r->d_tw + twoff[c], kClasses[c].n, kClasses[c].radix, kClasses[c].nstages, 0) !=
-            cudaSuccess)
-            st = GBFFT_ERR_CUDA;
+    for (size_t c = 0; st == GBFFT_OK && c < r->lens.size(); ++c) {
+        const RaggedLenState& L = r->lens[c];
+        for (size_t k = 0; st == GBFFT_OK && k < L.cands.size(); ++k)
+            if (launch_stage_twiddles(r->d_tw + L.tw_base[k], L.n, L.cands[k].data(), (int)L.cands[k].size(), 0) !=
+                cudaSuccess)
+                st = GBFFT_ERR_CUDA;
     }
-    if (st == GBFFT_OK &&
-        cudaMemcpy(r->d_twoff, twoff.data(), sizeof(int) * kRaggedCases, cudaMemcpyHostToDevice) != cudaSuccess)
-        st = GBFFT_ERR_CUDA;
     if (st == GBFFT_OK) {
         const void* ks[2] = {ragged_kernel_fwd(), ragged_kernel_inv()};
         int dev = 0, sms = 0, per_sm = 0;
         for (const void* k : ks)
-            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, r->smem) != cudaSuccess)
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRaggedSmemBytes) !=
+                cudaSuccess)
                 st = GBFFT_ERR_CUDA;
         if (st == GBFFT_OK &&
             (cudaGetDevice(&dev) != cudaSuccess ||
              cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks[0], kRaggedThreads, (size_t)r->smem) !=
-                 cudaSuccess ||
+             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks[0], kRaggedThreads,
+                                                           (size_t)kRaggedSmemBytes) != cudaSuccess ||
              per_sm < 1))
             st = GBFFT_ERR_CUDA;
         r->grid = per_sm * sms;
@@ -293,15 +378,12 @@ gbfft_status ragged_execute(RaggedState* r, int direction, const void* in, void*
     } else if (in != r->g_in || out != r->g_out) {
         cudaKernelNodeParams kp;
         if (cudaGraphKernelNodeGetParams(r->knode, &kp) != cudaSuccess) return GBFFT_ERR_CUDA;
+        // kernelParams points at copies owned by the graph node; build fresh ones.
         const float2* pin = (const float2*)in;
         float2* pout = (float2*)out;
-        void** a = kp.kernelParams;
-        // kernelParams points at copies owned by the graph node; build fresh ones.
         int nitems = (int)r->items.size();
-        void* args[] = {(void*)&pin, (void*)&pout, (void*)&r->d_items, (void*)&nitems, (void*)&r->d_offs,
-                        (void*)&r->d_tw,  (void*)&r->d_twoff, (void*)&r->d_counter, (void*)&status,
-                        (void*)&r->wait_ns};
-        (void)a;
+        void* args[10];
+        ragged_args(r, &pin, &pout, &nitems, &status, args);
         kp.kernelParams = args;
         if (cudaGraphExecKernelNodeSetParams(r->exec, r->knode, &kp) != cudaSuccess ||
             cudaGraphKernelNodeSetParams(r->knode, &kp) != cudaSuccess)
@@ -333,11 +415,11 @@ void ragged_set_wait_ns(RaggedState* r, long long ns) {
     ragged_release_graph(r);  // the limit is a kernel argument baked into the graph
 }
 
-// Autotuner: queue order, then coordinate descent over the rows-per-item
-// split of each class (1, 2, 4, 8), heaviest classes first, then each
-// length's compiled alternative radix schedules, timing the whole direct
-// launch with CUDA events (median of `reps`).  Keeps the best choices and
-// rebuilds the queue; the graph is re-captured on the next execute.
+// Autotuner: queue order, then per length, heaviest first, the tile shape
+// (rows per item = (8192/n)/split, split 1, 2, 4, 8), the candidate radix
+// schedules and the shared-memory padding, by coordinate descent, timing the
+// whole direct launch with CUDA events (median of `reps`).  Keeps the best
+// choices and rebuilds the queue; the graph is re-captured on the next execute.
 gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void* out, int* status, int reps,
                              float* best_ms) {
     cudaStream_t s;
@@ -365,58 +447,28 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
     if (reps < 1) reps = 1;
     float best = 0.f;
     gbfft_status st = measure(&best);
-    {
-        const int keep = r->order;
-        r->order = 1 - keep;
+    // Try one setting of one knob; keep it if faster, else restore.
+    auto trial = [&](int* knob, int value) {
+        if (st != GBFFT_OK || *knob == value) return;
+        const int keep = *knob;
+        *knob = value;
         float ms = 0.f;
-        if (st == GBFFT_OK) st = measure(&ms);
+        st = measure(&ms);
         if (st == GBFFT_OK && ms < best) best = ms;
-        else r->order = keep;
-    }
+        else *knob = keep;
+    };
+    trial(&r->order, 1 - r->order);
     std::vector<int> order;
-    for (int c = 0; c < kRaggedCases; ++c)
-        if (!r->members[c].empty()) order.push_back(c);
+    for (int c = 0; c < (int)r->lens.size(); ++c) order.push_back(c);
     std::sort(order.begin(), order.end(), [&](int a, int b) {
-        return (double)r->members[a].size() * kClasses[a].n > (double)r->members[b].size() * kClasses[b].n;
+        return (double)r->lens[a].members.size() * r->lens[a].n > (double)r->lens[b].members.size() * r->lens[b].n;
     });
     for (int c : order) {
-        if (st != GBFFT_OK) break;
-        const int keep = r->split[c];
-        int best_split = keep;
-        for (int sp : {1, 2, 4, 8}) {
-            if (sp == keep || kClasses[c].t / sp < 1) continue;
-            r->split[c] = sp;
-            float ms = 0.f;
-            st = measure(&ms);
-            if (st != GBFFT_OK) break;
-            if (ms < best) {
-                best = ms;
-                best_split = sp;
-            }
-        }
-        r->split[c] = best_split;
-    }
-    // Radix schedule per length: move a length's transforms to each compiled
-    // alternative case and keep the fastest.
-    std::vector<int64_t> tuned;
-    for (int c = 0; st == GBFFT_OK && c < kRaggedCases; ++c) {
-        if (r->members[c].empty()) continue;
-        if (std::find(tuned.begin(), tuned.end(), kClasses[c].n) != tuned.end()) continue;
-        tuned.push_back(kClasses[c].n);
-        int cur = c;
-        for (int a = 0; a < kRaggedCases && st == GBFFT_OK; ++a) {
-            if (a == cur || kClasses[a].n != kClasses[c].n || !r->members[a].empty()) continue;
-            r->members[a].swap(r->members[cur]);
-            if (kClasses[a].t == kClasses[cur].t) r->split[a] = r->split[cur];  // same tile shape
-            float ms = 0.f;
-            st = measure(&ms);
-            if (st == GBFFT_OK && ms < best) {
-                best = ms;
-                cur = a;
-            } else {
-                r->members[cur].swap(r->members[a]);
-            }
-        }
+        RaggedLenState& L = r->lens[c];
+        for (int sp : {1, 2, 4, 8})
+            if ((int64_t)kRaggedTile / L.n / sp >= 1) trial(&L.split, sp);
+        for (int k = 0; k < (int)L.cands.size(); ++k) trial(&L.cand, k);
+        trial(&L.ps, L.ps == kRaggedNoPad ? 4 : kRaggedNoPad);
     }
     if (st == GBFFT_OK) st = ragged_build_items(r);
     ragged_release_graph(r);
@@ -430,25 +482,30 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
 
 int ragged_queue_order(const RaggedState* r) { return r->order; }
 
-// The case currently used for length n (the one holding its transforms).
-static int case_in_use(const RaggedState* r, int64_t n) {
-    for (int c = 0; c < kRaggedCases; ++c)
-        if (kClasses[c].n == n && !r->members[c].empty()) return c;
-    return -1;
+static const RaggedLenState* len_state(const RaggedState* r, int64_t n) {
+    for (const RaggedLenState& L : r->lens)
+        if (L.n == n) return &L;
+    return nullptr;
 }
 
 int ragged_class_split(const RaggedState* r, int64_t n) {
-    const int c = case_in_use(r, n);
-    return c < 0 ? 0 : r->split[c];
+    const RaggedLenState* L = len_state(r, n);
+    return L ? L->split : 0;
 }
 
 int ragged_schedule(const RaggedState* r, int64_t n, int* radix) {
-    const int c = case_in_use(r, n);
-    if (c < 0) return 0;
-    for (int i = 0; i < kClasses[c].nstages; ++i) radix[i] = kClasses[c].radix[i];
-    return kClasses[c].nstages;
+    const RaggedLenState* L = len_state(r, n);
+    if (!L) return 0;
+    const std::vector<int>& sch = L->cands[L->cand];
+    for (size_t i = 0; i < sch.size(); ++i) radix[i] = sch[i];
+    return (int)sch.size();
 }
 
-bool ragged_supported(int64_t n) { return class_of(n) >= 0; }
+bool ragged_supported(int64_t n) {
+    if (n < 1 || n > kRaggedMaxN) return false;
+    for (int p : {2, 3, 5, 7})
+        while (n % p == 0) n /= p;
+    return n == 1;
+}
 
 }  // namespace gbfft

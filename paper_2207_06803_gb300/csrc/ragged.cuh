@@ -1,13 +1,19 @@
 // Ragged batches: thousands of transforms of uneven lengths in one persistent launch.
 //
-// The host groups the transforms by length ("class"), cuts each group into
-// work items of at most T_c rows (the tile shape of class c, chosen by the
-// autotuner), orders the items longest-first and uploads them with the list of
-// row offsets.  Each CTA of the persistent kernel repeatedly claims the next
-// item with one atomic increment and runs the class's Stockham schedule on it
-// (the same stage code as the single-pass kernel, with per-row offsets held in
-// shared memory), until the queue is empty.  Every class uses 256 threads per
-// CTA, so one kernel serves all classes.
+// The host groups the transforms by length, gives each length a radix schedule
+// (a Stockham factorisation n = R_1 ... R_t over the radices 2, 3, 4, 5, 7, 8,
+// 16), cuts each group into work items of at most T rows (T * n <= 8192
+// complex elements), orders the items and uploads them with the list of row
+// offsets and one descriptor per length.  Each CTA of the persistent kernel
+// repeatedly claims the next item with one atomic increment and runs the
+// item's schedule stage by stage: the first stage reads the rows straight from
+// HBM, stages exchange through a shared-memory tile, the last stage writes
+// straight to HBM (the stage algebra of the single-pass kernel, Eq. 2, with
+// the schedule read at run time instead of compiled per length).  Because
+// only the radix is compiled (one code path per radix and stage position), a
+// single kernel serves every length n <= 8192 whose prime factors are 2, 3, 5
+// and 7, with a small instruction footprint and without the register pressure
+// of per-length fully unrolled schedules.
 //
 // Items carry a `ready` word.  The host publishes all items ready; a CTA that
 // claims an item still marked not ready waits for it with a bounded spin
@@ -17,95 +23,42 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "codelets.cuh"
 #include "gbfft.h"
-#include "stockham.cuh"
 
 namespace gbfft {
 
-constexpr int kRaggedThreads = 256;
+constexpr int kRaggedThreads = 512;    // threads per CTA
+constexpr int kRaggedTile = 8192;      // complex elements per item at most (T * n)
+constexpr int kRaggedMaxRows = 512;    // rows per item at most
+constexpr int kRaggedMaxStages = 8;
+constexpr int kRaggedMaxN = 8192;
+constexpr int kRaggedNoPad = 31;       // pad shift meaning "no padding"
+// Shared-memory tile with the densest padding allowed (one slot per 16).
+constexpr int kRaggedSmemBytes = (int)sizeof(float2) * (kRaggedTile + kRaggedTile / 16);
 
 struct RaggedItem {
-    int cls;    // class index (length) in the class table
-    int count;  // rows in this item (<= T of the class)
+    int cls;    // index of the item's length descriptor
+    int count;  // rows in this item (<= T of the length)
     int first;  // index of the item's first row offset in the offset list
     int ready;  // nonzero once the item may be processed
 };
 
-// (case index, N, T rows per full tile, shared-memory pad shift, radix
-// schedule...).  Every class runs kRaggedThreads threads; T is about
-// 4096/N (at most 256) so a tile holds ~4096 elements and each thread at most
-// 32 complex values; a stage with fewer butterflies than threads leaves some
-// idle.
-#define GBFFT_RAGGED_CLASSES(X)               \
-    X(0, 8, 256, 4, 2, 4)                     \
-    X(1, 10, 256, 0, 5, 2)                    \
-    X(2, 12, 256, 0, 3, 4)                    \
-    X(3, 14, 256, 0, 7, 2)                    \
-    X(4, 16, 256, 4, 4, 4)                    \
-    X(5, 20, 204, 0, 5, 4)                    \
-    X(6, 24, 170, 0, 3, 8)                    \
-    X(7, 28, 146, 0, 7, 4)                    \
-    X(8, 32, 128, 4, 4, 8)                    \
-    X(9, 40, 102, 0, 5, 8)                    \
-    X(10, 48, 85, 4, 3, 16)                   \
-    X(11, 56, 73, 0, 7, 8)                    \
-    X(12, 64, 64, 4, 8, 8)                    \
-    X(13, 80, 51, 5, 5, 16)                   \
-    X(14, 96, 42, 4, 3, 2, 16)                \
-    X(15, 112, 36, 4, 7, 16)                  \
-    X(16, 128, 32, 4, 8, 16)                  \
-    X(17, 160, 25, 0, 5, 2, 16)               \
-    X(18, 192, 21, 0, 3, 4, 16)               \
-    X(19, 224, 18, 0, 7, 2, 16)               \
-    X(20, 256, 16, 4, 16, 16)                 \
-    X(21, 320, 12, 0, 5, 4, 16)               \
-    X(22, 384, 10, 0, 3, 8, 16)               \
-    X(23, 448, 9, 0, 7, 4, 16)                \
-    X(24, 512, 8, 4, 2, 16, 16)               \
-    X(25, 640, 6, 0, 5, 8, 16)                \
-    X(26, 768, 5, 4, 3, 16, 16)               \
-    X(27, 896, 4, 0, 7, 8, 16)                \
-    X(28, 1024, 4, 4, 4, 16, 16)              \
-    X(29, 1280, 3, 5, 5, 16, 16)              \
-    X(30, 1536, 2, 4, 3, 16, 16, 2)           \
-    X(31, 1792, 2, 4, 7, 16, 16)              \
-    X(32, 2048, 2, 4, 16, 16, 8)              \
-    X(33, 2560, 1, 5, 5, 16, 16, 2)           \
-    X(34, 3072, 1, 4, 3, 16, 16, 4)           \
-    X(35, 3584, 1, 4, 7, 16, 16, 2)           \
-    X(36, 4096, 1, 4, 16, 16, 16)             \
-    X(37, 5120, 1, 4, 5, 16, 16, 4)           \
-    X(38, 6144, 1, 4, 3, 16, 16, 8)           \
-    X(39, 7168, 1, 4, 7, 16, 16, 4)           \
-    X(40, 8192, 1, 4, 16, 16, 32)             \
-    X(41, 256, 16, 4, 4, 8, 8)                \
-    X(42, 512, 8, 4, 8, 8, 8)                 \
-    X(43, 1024, 4, 4, 16, 16, 4)              \
-    X(44, 2048, 2, 4, 8, 16, 16)              \
-    X(45, 4096, 1, 4, 8, 8, 8, 8)             \
-    X(46, 8192, 1, 4, 16, 16, 16, 2)          \
-    X(47, 3072, 1, 4, 3, 8, 8, 8, 2)          \
-    X(48, 128, 32, 4, 2, 8, 8)                \
-    X(49, 20, 102, 0, 5, 4)                   \
-    X(50, 24, 85, 0, 3, 8)                    \
-    X(51, 28, 73, 0, 7, 4)                    \
-    X(52, 40, 51, 0, 5, 8)                    \
-    X(53, 48, 42, 4, 3, 16)                   \
-    X(54, 56, 36, 0, 7, 8)                    \
-    X(55, 80, 25, 5, 5, 16)                   \
-    X(56, 96, 21, 4, 3, 2, 16)                \
-    X(57, 112, 18, 4, 7, 16)                  \
-    X(58, 160, 12, 0, 5, 2, 16)               \
-    X(59, 192, 10, 0, 3, 4, 16)               \
-    X(60, 224, 9, 0, 7, 2, 16)                \
-    X(61, 448, 4, 0, 7, 4, 16)
+// One stage of a length's schedule: radix R, L = R_1 ... R_{s-1}, n/R
+// butterflies per row, offset of the stage's twiddle block
+// W[(q-1)*L + k] = w_{L R}^(q k) in the plan's table (used when L > 1), and
+// the reciprocals that turn the two divisions of the index arithmetic into
+// multiplications.
+struct RaggedStage {
+    int r, l, nr, tw;
+    float rcp_nr, rcp_l;
+};
 
-// Compiled cases: the first case of each length (indices 0..40) is its default
-// schedule; cases 41.. are alternatives the autotuner may choose: other radix
-// schedules (41-48) and half-height tiles, whose smaller per-thread register
-// arrays avoid spills for the odd-radix lengths (49-61).
-constexpr int kRaggedCases = 62;
-
+struct RaggedLen {
+    int n, nstages, ps;  // ps: shared-memory pad shift (kRaggedNoPad: none)
+    float rcp_n;         // 1/n
+    RaggedStage st[kRaggedMaxStages];
+};
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -113,33 +66,120 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-template <int S, int N, int T, int PS, int... Rs>
-__device__ __noinline__ void ragged_item(const float2* in, float2* out, const long long* s_off, float2* sm,
-                                            const float2* __restrict__ tw, int nvalid) {
-    constexpr int TPB = kRaggedThreads;
-    constexpr int E = capacity_of_r<N, T, TPB, Rs...>();
-    static_assert(T >= 1 && T <= kRaggedThreads && E <= 32, "class tile shape");
-    const IndexedIO<N> io{in, out, s_off};
-    float2 v[E];
-    gather_global<N, E, T, First<Rs...>::value, IndexedIO<N>, TPB>(v, io, nvalid);
-    run_stages_t<N, S, E, T, PS, TPB, true, 0, 1, Rs...>(v, io, sm, tw, nvalid);
+// floor(x / d) for 0 <= x < 2^22 - 1, from rcp = fl(1/d), d >= 1: the exact
+// quotient (x + 1/2)/d lies at least 1/(2d) from every integer, and the two
+// roundings move it by at most (x + 1/2)/d * 2^-23 < 1/(2d), so truncation
+// gives the integer part exactly.
+__device__ __forceinline__ int rdiv(int x, float rcp) { return __float2int_rz(__fmul_rn((float)x + 0.5f, rcp)); }
+
+__device__ __forceinline__ int rpad(int i, int ps) { return i + (i >> ps); }
+
+// An opaque copy of x: index arithmetic derived from it is recomputed where it
+// is needed instead of being kept live in registers across a stage.
+__device__ __forceinline__ int opaque(int x) {
+    asm volatile("" : "+r"(x));
+    return x;
+}
+
+// Butterflies of radix R per thread when the tile holds at most kRaggedTile elements.
+template <int R>
+constexpr int ragged_nb() {
+    return (kRaggedTile / R + kRaggedThreads - 1) / kRaggedThreads;
+}
+
+// One stage on the item's `count` rows: operands from the shared tile
+// (src_smem) or from the rows in HBM, results to the shared tile (dst_smem)
+// or to the rows in HBM (only the last stage, where L*R = n so the write
+// index b*L*R + q*L + k reduces to q*L + j).  The code is branch-free in the
+// butterfly index: threads past the stage's last butterfly recompute that
+// butterfly and store the same values to the same places, which keeps every
+// per-butterfly guard (and the register pressure that divergent regions
+// bring) out of the unrolled loops.  A duplicate may re-read an HBM row only
+// in the first stage, before any stage of the item has written its output.
+template <int S, int R>
+__device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const float2* in, float2* out,
+                                             const long long* s_off, float2* sm, const float2* __restrict__ tw,
+                                             const RaggedStage& st, int n, int ps, int count) {
+    constexpr int NB = ragged_nb<R>();
+    const int nr = st.nr, L = st.l;
+    const int last = count * nr - 1;  // index of the stage's last butterfly
+    const int tid = threadIdx.x;
+    float2 v[NB * R];
+    if (src_smem) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int B = min(tid + u * kRaggedThreads, last);
+            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const int base = t * n + j;
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[u * R + q] = sm[rpad(base + q * nr, ps)];
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int B = min(tid + u * kRaggedThreads, last);
+            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const float2* p = in + s_off[t] + j;
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[u * R + q] = p[q * nr];
+        }
+    }
+    if (L > 1) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int B = min(opaque(tid + u * kRaggedThreads), last);
+            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const int k = j - rdiv(j, st.rcp_l) * L;
+            const float2* w = tw + st.tw + k;
+#pragma unroll
+            for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], __ldg(w + (q - 1) * L));
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NB; ++u) Dft<S, R>::run(&v[u * R]);
+    if (dst_smem) {
+        if (src_smem) __syncthreads();  // every read of the tile precedes the first write
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int B = min(opaque(tid + u * kRaggedThreads), last);
+            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const int b = rdiv(j, st.rcp_l), k = j - b * L;
+            const int base = t * n + b * L * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) sm[rpad(base + q * L, ps)] = v[u * R + q];
+        }
+        __syncthreads();
+    } else {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int B = min(opaque(tid + u * kRaggedThreads), last);
+            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            float2* p = out + s_off[t] + j;
+#pragma unroll
+            for (int q = 0; q < R; ++q) p[q * L] = v[u * R + q];
+        }
+    }
 }
 
 template <int S>
-__global__ void __launch_bounds__(kRaggedThreads, 3) k_ragged(const float2* in, float2* out, const RaggedItem* items,
+__global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, float2* out, const RaggedItem* items,
                                                            int nitems, const long long* offs,
-                                                           const float2* __restrict__ tw,
-                                                           const int* __restrict__ tw_off, int* counter, int* status,
+                                                           const RaggedLen* __restrict__ lens,
+                                                           const float2* __restrict__ tw, int* counter, int* status,
                                                            long long wait_ns) {
     extern __shared__ float2 sm[];
-    __shared__ long long s_off[kRaggedThreads];
+    __shared__ long long s_off[kRaggedMaxRows];
+    __shared__ RaggedLen s_len;
     __shared__ int s_item, s_ok;
+    int next = 0;  // thread 0: the item claimed for the next round
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
     for (;;) {
-        __syncthreads();  // the previous item's readers of s_off and sm are done
+        __syncthreads();  // the previous item's readers of s_off, s_len and sm are done
         if (threadIdx.x == 0) {
-            const int it = atomicAdd(counter, 1);
+            const int it = next;
             int ok = 1;
             if (it < nitems) {
+                next = atomicAdd(counter, 1);  // claimed now, used next round: the latency overlaps this item
                 const volatile int* rdy = &items[it].ready;
                 if (*rdy == 0) {
                     const unsigned long long t0 = globaltimer_ns();
@@ -162,18 +202,42 @@ __global__ void __launch_bounds__(kRaggedThreads, 3) k_ragged(const float2* in, 
         if (!s_ok) continue;
         const RaggedItem d = items[it];
         for (int t = threadIdx.x; t < d.count; t += kRaggedThreads) s_off[t] = offs[d.first + t];
+        {
+            const int* src = reinterpret_cast<const int*>(lens + d.cls);
+            int* dst = reinterpret_cast<int*>(&s_len);
+            for (int w = threadIdx.x; w < (int)(sizeof(RaggedLen) / sizeof(int)); w += kRaggedThreads)
+                dst[w] = __ldg(src + w);
+        }
         __syncthreads();
-        const float2* twc = tw + tw_off[d.cls];
-        switch (d.cls) {
-#define GBFFT_RAGGED_CASE(idx, N, T, PS, ...)                                      \
-    case idx:                                                                     \
-        ragged_item<S, N, T, PS, __VA_ARGS__>(in, out, s_off, sm, twc, d.count); \
-        break;
-            GBFFT_RAGGED_CLASSES(GBFFT_RAGGED_CASE)
-#undef GBFFT_RAGGED_CASE
-            default:
-                if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
-                break;
+        const int n = s_len.n, ns = s_len.nstages, ps = s_len.ps;
+        if (ns == 0) {  // n == 1: DFT_1 is the identity
+            for (int t = threadIdx.x; t < d.count; t += kRaggedThreads) out[s_off[t]] = in[s_off[t]];
+            continue;
+        }
+        // A one-stage schedule (n <= 16) also goes through the tile, then a
+        // copy writes the rows out, so that no stage reads and writes HBM.
+        for (int s = 0; s < ns; ++s) {
+            const RaggedStage st = s_len.st[s];
+            const bool src_smem = s > 0, dst_smem = s < ns - 1 || ns == 1;
+            switch (st.r) {
+                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                default:
+                    if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
+                    break;
+            }
+        }
+        if (ns == 1) {
+            const float rcp_n = s_len.rcp_n;
+            for (int idx = threadIdx.x; idx < d.count * n; idx += kRaggedThreads) {
+                const int t = rdiv(idx, rcp_n), j = idx - t * n;
+                out[s_off[t] + j] = sm[rpad(idx, ps)];
+            }
         }
     }
 }
