@@ -62,14 +62,6 @@ std::vector<std::vector<int>> schedules_of(int64_t n) {
     return out;
 }
 
-// Default shared-memory pad shift: one slot per 16 for lengths whose odd part
-// is 1 or 3 (their exchanges stride by powers of two), none otherwise.
-int default_pad(int64_t n) {
-    int64_t m = n;
-    while (m % 2 == 0) m /= 2;
-    return (m == 1 || m == 3) ? 4 : kRaggedNoPad;
-}
-
 }  // namespace
 
 struct RaggedLenState {
@@ -79,7 +71,6 @@ struct RaggedLenState {
     std::vector<int> tw_base;                   // twiddle-table offset of each candidate
     int cand = 0;                               // schedule in use
     int split = 1;                              // tile shape: rows per item = (8192 / n) / split
-    int ps = kRaggedNoPad;                      // shared-memory pad shift
 };
 
 struct RaggedState {
@@ -134,8 +125,7 @@ static RaggedLen describe(const RaggedLenState& L) {
     const std::vector<int>& sch = L.cands[L.cand];
     d.n = (int)L.n;
     d.nstages = (int)sch.size();
-    d.ps = L.ps;
-    d.rcp_n = 1.0f / (float)L.n;
+    d.mag_n = ragged_magic((int)L.n);
     int l = 1, tw = L.tw_base[L.cand];
     for (int s = 0; s < d.nstages; ++s) {
         RaggedStage& st = d.st[s];
@@ -143,8 +133,8 @@ static RaggedLen describe(const RaggedLenState& L) {
         st.l = l;
         st.nr = (int)L.n / sch[s];
         st.tw = tw;
-        st.rcp_nr = 1.0f / (float)st.nr;
-        st.rcp_l = 1.0f / (float)l;
+        st.mag_nr = ragged_magic(st.nr);
+        st.mag_l = ragged_magic(l);
         if (l > 1) tw += (sch[s] - 1) * l;
         l *= sch[s];
     }
@@ -289,7 +279,6 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
         RaggedLenState& L = r->lens[c];
         L.n = distinct[c];
         L.cands = schedules_of(L.n);
-        L.ps = default_pad(L.n);
         for (const auto& sch : L.cands) {
             L.tw_base.push_back(tw_total);
             tw_total += stage_twiddle_count(sch.data(), (int)sch.size());
@@ -416,8 +405,8 @@ void ragged_set_wait_ns(RaggedState* r, long long ns) {
 }
 
 // Autotuner: queue order, then per length, heaviest first, the tile shape
-// (rows per item = (8192/n)/split, split 1, 2, 4, 8), the candidate radix
-// schedules and the shared-memory padding, by coordinate descent, timing the
+// (rows per item = (8192/n)/split, split 1, 2, 4, 8) and the candidate radix
+// schedules, by coordinate descent, timing the
 // whole direct launch with CUDA events (median of `reps`).  Keeps the best
 // choices and rebuilds the queue; the graph is re-captured on the next execute.
 gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void* out, int* status, int reps,
@@ -468,7 +457,6 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
         for (int sp : {1, 2, 4, 8})
             if ((int64_t)kRaggedTile / L.n / sp >= 1) trial(&L.split, sp);
         for (int k = 0; k < (int)L.cands.size(); ++k) trial(&L.cand, k);
-        trial(&L.ps, L.ps == kRaggedNoPad ? 4 : kRaggedNoPad);
     }
     if (st == GBFFT_OK) st = ragged_build_items(r);
     ragged_release_graph(r);

@@ -33,8 +33,8 @@ constexpr int kRaggedTile = 8192;      // complex elements per item at most (T *
 constexpr int kRaggedMaxRows = 512;    // rows per item at most
 constexpr int kRaggedMaxStages = 8;
 constexpr int kRaggedMaxN = 8192;
-constexpr int kRaggedNoPad = 31;       // pad shift meaning "no padding"
-// Shared-memory tile with the densest padding allowed (one slot per 16).
+// Shared-memory tile with one padding slot per 16 complex (spreads the
+// power-of-two strides of the exchanges across banks).
 constexpr int kRaggedSmemBytes = (int)sizeof(float2) * (kRaggedTile + kRaggedTile / 16);
 
 struct RaggedItem {
@@ -47,18 +47,27 @@ struct RaggedItem {
 // One stage of a length's schedule: radix R, L = R_1 ... R_{s-1}, n/R
 // butterflies per row, offset of the stage's twiddle block
 // W[(q-1)*L + k] = w_{L R}^(q k) in the plan's table (used when L > 1), and
-// the reciprocals that turn the two divisions of the index arithmetic into
-// multiplications.
+// the multipliers (ragged_magic) that turn the two divisions of the index
+// arithmetic into one multiply-high each.
 struct RaggedStage {
     int r, l, nr, tw;
-    float rcp_nr, rcp_l;
+    unsigned mag_nr, mag_l;
 };
 
 struct RaggedLen {
-    int n, nstages, ps;  // ps: shared-memory pad shift (kRaggedNoPad: none)
-    float rcp_n;         // 1/n
+    int n, nstages;
+    unsigned mag_n;
+    int pad;
     RaggedStage st[kRaggedMaxStages];
 };
+
+// Division by an invariant integer with a multiply-high (the method of
+// Granlund and Montgomery, 1994): with m = ceil(2^31 / d),
+// floor(x / d) = floor(2x * m / 2^32) for 0 <= x < 2^31 / d.  Writing
+// x = q d + r, 2x m / 2^32 = q + (r + x e / 2^31) / d with e = m d - 2^31 < d,
+// and r + x e / 2^31 < d whenever x e < 2^31.  Every dividend here is below
+// 8192 and every divisor at most 8192.
+inline unsigned ragged_magic(int d) { return (unsigned)(((1ull << 31) + (unsigned long long)d - 1) / (unsigned)d); }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -66,20 +75,10 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// floor(x / d) for 0 <= x < 2^22 - 1, from rcp = fl(1/d), d >= 1: the exact
-// quotient (x + 1/2)/d lies at least 1/(2d) from every integer, and the two
-// roundings move it by at most (x + 1/2)/d * 2^-23 < 1/(2d), so truncation
-// gives the integer part exactly.
-__device__ __forceinline__ int rdiv(int x, float rcp) { return __float2int_rz(__fmul_rn((float)x + 0.5f, rcp)); }
+__device__ __forceinline__ int rdiv(int x, unsigned m) { return (int)__umulhi((unsigned)x << 1, m); }
 
-__device__ __forceinline__ int rpad(int i, int ps) { return i + (i >> ps); }
+__device__ __forceinline__ int rpad(int i) { return i + (i >> 4); }
 
-// An opaque copy of x: index arithmetic derived from it is recomputed where it
-// is needed instead of being kept live in registers across a stage.
-__device__ __forceinline__ int opaque(int x) {
-    asm volatile("" : "+r"(x));
-    return x;
-}
 
 // Butterflies of radix R per thread when the tile holds at most kRaggedTile elements.
 template <int R>
@@ -99,7 +98,7 @@ constexpr int ragged_nb() {
 template <int S, int R>
 __device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const float2* in, float2* out,
                                              const long long* s_off, float2* sm, const float2* __restrict__ tw,
-                                             const RaggedStage& st, int n, int ps, int count) {
+                                             const RaggedStage& st, int n, int count) {
     constexpr int NB = ragged_nb<R>();
     const int nr = st.nr, L = st.l;
     const int last = count * nr - 1;  // index of the stage's last butterfly
@@ -109,16 +108,16 @@ __device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int B = min(tid + u * kRaggedThreads, last);
-            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const int t = rdiv(B, st.mag_nr), j = B - t * nr;
             const int base = t * n + j;
 #pragma unroll
-            for (int q = 0; q < R; ++q) v[u * R + q] = sm[rpad(base + q * nr, ps)];
+            for (int q = 0; q < R; ++q) v[u * R + q] = sm[rpad(base + q * nr)];
         }
     } else {
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int B = min(tid + u * kRaggedThreads, last);
-            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const int t = rdiv(B, st.mag_nr), j = B - t * nr;
             const float2* p = in + s_off[t] + j;
 #pragma unroll
             for (int q = 0; q < R; ++q) v[u * R + q] = p[q * nr];
@@ -127,9 +126,9 @@ __device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const
     if (L > 1) {
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
-            const int B = min(opaque(tid + u * kRaggedThreads), last);
-            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
-            const int k = j - rdiv(j, st.rcp_l) * L;
+            const int B = min(tid + u * kRaggedThreads, last);
+            const int t = rdiv(B, st.mag_nr), j = B - t * nr;
+            const int k = j - rdiv(j, st.mag_l) * L;
             const float2* w = tw + st.tw + k;
 #pragma unroll
             for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], __ldg(w + (q - 1) * L));
@@ -141,19 +140,19 @@ __device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const
         if (src_smem) __syncthreads();  // every read of the tile precedes the first write
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
-            const int B = min(opaque(tid + u * kRaggedThreads), last);
-            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
-            const int b = rdiv(j, st.rcp_l), k = j - b * L;
+            const int B = min(tid + u * kRaggedThreads, last);
+            const int t = rdiv(B, st.mag_nr), j = B - t * nr;
+            const int b = rdiv(j, st.mag_l), k = j - b * L;
             const int base = t * n + b * L * R + k;
 #pragma unroll
-            for (int q = 0; q < R; ++q) sm[rpad(base + q * L, ps)] = v[u * R + q];
+            for (int q = 0; q < R; ++q) sm[rpad(base + q * L)] = v[u * R + q];
         }
         __syncthreads();
     } else {
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
-            const int B = min(opaque(tid + u * kRaggedThreads), last);
-            const int t = rdiv(B, st.rcp_nr), j = B - t * nr;
+            const int B = min(tid + u * kRaggedThreads, last);
+            const int t = rdiv(B, st.mag_nr), j = B - t * nr;
             float2* p = out + s_off[t] + j;
 #pragma unroll
             for (int q = 0; q < R; ++q) p[q * L] = v[u * R + q];
@@ -209,7 +208,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
                 dst[w] = __ldg(src + w);
         }
         __syncthreads();
-        const int n = s_len.n, ns = s_len.nstages, ps = s_len.ps;
+        const int n = s_len.n, ns = s_len.nstages;
         if (ns == 0) {  // n == 1: DFT_1 is the identity
             for (int t = threadIdx.x; t < d.count; t += kRaggedThreads) out[s_off[t]] = in[s_off[t]];
             continue;
@@ -220,23 +219,23 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
             const RaggedStage st = s_len.st[s];
             const bool src_smem = s > 0, dst_smem = s < ns - 1 || ns == 1;
             switch (st.r) {
-                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
-                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
-                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
-                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
-                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
-                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
-                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, ps, d.count); break;
+                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
                 default:
                     if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
                     break;
             }
         }
         if (ns == 1) {
-            const float rcp_n = s_len.rcp_n;
+            const unsigned mag_n = s_len.mag_n;
             for (int idx = threadIdx.x; idx < d.count * n; idx += kRaggedThreads) {
-                const int t = rdiv(idx, rcp_n), j = idx - t * n;
-                out[s_off[t] + j] = sm[rpad(idx, ps)];
+                const int t = rdiv(idx, mag_n), j = idx - t * n;
+                out[s_off[t] + j] = sm[rpad(idx)];
             }
         }
     }
