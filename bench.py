@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
-    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving"], default="sweep",
+    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving", "f64"], default="sweep",
                     help="sweep (default, the headline line) or one of the other configurations")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -433,7 +433,7 @@ def other_configs(args):
     small = argparse.Namespace(**vars(args))
     small.steps = 40
     for name, fn in (("twopass", run_twopass), ("tc", lambda a: run_tc(a, dists=("uniform",))),
-                     ("ragged", run_ragged),
+                     ("ragged", run_ragged), ("f64", run_f64),
                      ("serving", lambda a: run_serving(a, rates=(1000, 10000), scale=0.2, serial_rates=(1000,)))):
         try:
             r = fn(small)
@@ -445,6 +445,9 @@ def other_configs(args):
         elif name == "tc":
             out[name] = {k: {"gbs": round(v["gbs"], 1), "vs_fp32": round(v["vs_fp32"], 3),
                              "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for k, v in r["results"].items()}
+        elif name == "f64":
+            out[name] = {n: {"fwd_gflops": round(v["fwd"]["gflops"], 1), "fwd_gbs": round(v["fwd"]["gbs"], 1),
+                             "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for n, v in r["per_size"].items()}
         elif name == "ragged":
             res = r["results"]
             out[name] = {k: res[k] for k in ("ragged_graph_tuned_us", "ragged_gbs", "per_size_us", "per_transform_us",
@@ -530,6 +533,53 @@ def run_twopass(args):
                         "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak}
     return {"config": "twopass", "metric": "two-pass Eq. 2 c2c GB/s (16 B/point algorithmic)",
             "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_size": rows}
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured figure exists for it)
+
+
+def run_f64(args):
+    """Complex128 / FP64 path: N = 2^3..2^12 (and three mixed lengths), forward and inverse,
+    2^26 points per call (1 GiB in, 1 GiB out); GB/s on 32 B/point, GFLOP/s on 5 N log2 N per
+    transform against the nominal FP64 peak (this path is bound by the FP64 pipe, not HBM)."""
+    import math
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    total = TOTAL
+    lo = synth.uniform_flat(synth.DEFAULT_SEED + 1, 0, total).astype(np.complex128)
+    flat = synth.uniform_flat(synth.DEFAULT_SEED, 0, total).astype(np.complex128) + lo * 2.0 ** -26
+    del lo
+    d_in = torch.from_numpy(flat.view(np.float64)).cuda()
+    d_out = torch.empty_like(d_in)
+    d_rt = torch.empty_like(d_in)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for n in [1 << k for k in range(3, 13)] + [1536, 2560, 3584]:
+        batch = total // n
+        res = {}
+        for direction, name in ((-1, "fwd"), (1, "inv")):
+            with gbfft.Plan(n, batch, direction, dtype=gbfft.GBFFT_C2C_F64) as p:
+                ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 30), stream)
+            flops = 5.0 * n * math.log2(n) * batch
+            res[name] = {"ms": ms, "gbs": 32.0 * n * batch / (ms * 1e-3) / 1e9,
+                         "gflops": flops / (ms * 1e-3) / 1e9,
+                         "frac_of_fp64_nominal": flops / (ms * 1e-3) / (FP64_NOMINAL_TFLOPS * 1e12)}
+        with gbfft.Plan(n, batch, -1, dtype=gbfft.GBFFT_C2C_F64) as pf, \
+                gbfft.Plan(n, batch, 1, dtype=gbfft.GBFFT_C2C_F64) as pi:
+            pf.execute(d_in, d_out, stream)
+            pi.execute(d_out, d_rt, stream)
+        torch.cuda.synchronize()
+        sample = torch.from_numpy(synth.sample_rows(synth.DEFAULT_SEED, batch, 256)).cuda()
+        a = d_rt[: 2 * n * batch].view(batch, 2 * n).index_select(0, sample).cpu().numpy().view(np.complex128)
+        b = d_in[: 2 * n * batch].view(batch, 2 * n).index_select(0, sample).cpu().numpy().view(np.complex128) * n
+        err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+        res["roundtrip_rel_l2_max"] = float(err.max())
+        rows[str(n)] = res
+    return {"config": "f64", "metric": "complex128 FP64 c2c GFLOP/s (5 N log2 N) and GB/s (32 B/point)",
+            "unit": "GFLOP/s", "points_per_call": total, "fp64_peak_tflops": FP64_NOMINAL_TFLOPS,
+            "fp64_peak_source": "nominal GB300 dense FP64", "per_size": rows}
 
 
 def run_tc(args, dists=("uniform", "gaussian_scaled")):
@@ -703,7 +753,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "sweep":
-        fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving}[args.config]
+        fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving,
+              "f64": run_f64}[args.config]
         print(json.dumps(fn(args)), flush=True)
         return 0
     return run_gpu(args)

@@ -59,7 +59,11 @@ typedef enum {
 typedef enum {
     GBFFT_C2C_F32 = 0,           /* complex64 in/out, FP32 arithmetic, FP64-generated twiddles */
     GBFFT_C2C_F32_TC_FP16X2 = 1, /* complex64 in/out; every DFT_16 block as FP16 hi+lo tensor-core products */
-    GBFFT_C2C_F32_TC_BF16X2 = 2  /* complex64 in/out; every DFT_16 block as BF16 hi+lo tensor-core products */
+    GBFFT_C2C_F32_TC_BF16X2 = 2, /* complex64 in/out; every DFT_16 block as BF16 hi+lo tensor-core products */
+    GBFFT_C2C_F64 = 3            /* complex128 in/out (interleaved double re, im; 16 bytes per point), FP64
+                                    arithmetic and FP64 twiddles, the paper's own precision (Sec. VI);
+                                    single pass, n = 2^a 3^b 5^c 7^d <= 4096 with at most one odd factor
+                                    (2^k, 3*2^k, 5*2^k, 7*2^k); relative L2 error ~1e-16*log2(n) */
 } gbfft_dtype;
 
 /* Human-readable name of a status code (static storage; never NULL). */

@@ -43,7 +43,7 @@ cudaError_t prepare_rows(const RowsVariant& v) {
     return e;
 }
 
-cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, float2* out, const float2* tw,
+cudaError_t launch_rows(const RowsVariant& v, int direction, const void* in, void* out, const void* tw,
                         long long batch, int grid_cap, cudaStream_t stream, int* status) {
     if (batch <= 0) return cudaSuccess;
     long long blocks = (batch + v.rows - 1) / v.rows;
@@ -71,6 +71,7 @@ struct gbfft_plan_s {
     const RowsVariant* rv = nullptr;
     int grid_cap = 0;  // persistent variants: resident CTAs on the device
     float2* tw = nullptr;
+    double2* tw64 = nullptr;  // complex128 plans: FP64 stage twiddles
     // two passes (Eq. 2 with N = K * M)
     int64_t k_outer = 1, m_inner = 0;
     const ColsVariant* cv_m = nullptr;  // pass 1: length-M columns
@@ -91,7 +92,7 @@ struct gbfft_plan_s {
     size_t ws_bytes = 0;
     // host-buffer execution: staging ring and its streams/events (created on first use)
     static constexpr int kRing = 3;
-    float2* stage[kRing] = {nullptr, nullptr, nullptr};
+    void* stage[kRing] = {nullptr, nullptr, nullptr};
     int64_t stage_rows = 0;
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t ev_start = nullptr, ev_in[kRing] = {}, ev_comp[kRing] = {}, ev_out[kRing] = {};
@@ -102,6 +103,9 @@ namespace {
 constexpr int kMaxVariantsPerSize = 16;
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Bytes per complex point of a dtype.
+size_t elem_bytes(int dtype) { return dtype == GBFFT_C2C_F64 ? sizeof(double2) : sizeof(float2); }
 
 gbfft_status check_io(const void* in, const void* out, size_t bytes) {
     if (!in || !out) return GBFFT_ERR_INVALID_ARG;
@@ -129,6 +133,7 @@ void free_plan(gbfft_plan p) {
     if (p->ragged) ragged_destroy(p->ragged);
     if (p->tc_frag) cudaFree(p->tc_frag);
     if (p->umma_b) cudaFree(p->umma_b);
+    if (p->tw64) cudaFree(p->tw64);
     float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
     for (float2* b : bufs)
         if (b) cudaFree(b);
@@ -218,13 +223,51 @@ gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction,
     return GBFFT_OK;
 }
 
+// Complex128 plan: one single-pass FP64 variant (no two-pass or tensor-core form).
+gbfft_status create_f64(gbfft_plan* out, int64_t n, int64_t batch, int direction, int variant, int64_t k_outer) {
+    if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
+    const RowsVariant* cands[kMaxVariantsPerSize];
+    const int nc = rows_variants_f64_for(n, cands, kMaxVariantsPerSize);
+    if (nc == 0) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    if (variant < 0) variant = 0;
+    if (variant >= nc) return GBFFT_ERR_NOT_FOUND;
+    gbfft_plan p = new (std::nothrow) gbfft_plan_s();
+    if (!p) return GBFFT_ERR_OOM;
+    p->kind = kPlanSingle;
+    p->n = n;
+    p->batch = batch;
+    p->direction = direction;
+    p->dtype = GBFFT_C2C_F64;
+    p->variant = variant;
+    p->rv = cands[variant];
+    gbfft_status st = GBFFT_OK;
+    const int cnt = stage_twiddle_count(p->rv->radix, p->rv->nstages);
+    if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->tw64, sizeof(double2) * (size_t)(cnt > 0 ? cnt : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        st = GBFFT_ERR_OOM;
+    }
+    if (st == GBFFT_OK && prepare_rows(*p->rv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && launch_stage_twiddles64(p->tw64, n, p->rv->radix, p->rv->nstages, 0) != cudaSuccess)
+        st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st != GBFFT_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return GBFFT_OK;
+}
+
 gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int variant,
                     int64_t k_outer) {
     if (!out) return GBFFT_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 1 || batch < 0 || k_outer < 0) return GBFFT_ERR_INVALID_ARG;
     if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
-    if (dtype != GBFFT_C2C_F32 && dtype != GBFFT_C2C_F32_TC_FP16X2 && dtype != GBFFT_C2C_F32_TC_BF16X2)
+    if (dtype != GBFFT_C2C_F32 && dtype != GBFFT_C2C_F32_TC_FP16X2 && dtype != GBFFT_C2C_F32_TC_BF16X2 &&
+        dtype != GBFFT_C2C_F64)
         return GBFFT_ERR_INVALID_ARG;
     if (variant < 0 && k_outer == 0) {  // no forced choice: use autotuned wisdom when there is some
         wisdom_load_env_once();
@@ -235,11 +278,14 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
                 int64_t kk, mm;
                 if (choose_split(n, wk, &kk, &mm)) k_outer = wk;
             } else if (wv >= 0) {
-                const int limit = dtype == GBFFT_C2C_F32 ? rows_variants_for(n, nullptr, 0) : 2;
+                const int limit = dtype == GBFFT_C2C_F32   ? rows_variants_for(n, nullptr, 0)
+                                  : dtype == GBFFT_C2C_F64 ? rows_variants_f64_for(n, nullptr, 0)
+                                                           : 2;
                 if (wv < limit) variant = wv;
             }
         }
     }
+    if (dtype == GBFFT_C2C_F64) return create_f64(out, n, batch, direction, variant, k_outer);
     if (dtype != GBFFT_C2C_F32) {
         if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
         if (variant > 1) return GBFFT_ERR_NOT_FOUND;
@@ -313,7 +359,11 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
 }
 
 // Enqueue the transform of `rows` rows from `in` to `out` (device pointers).
-cudaError_t run_device(gbfft_plan p, const float2* in, float2* out, int64_t rows, cudaStream_t s) {
+cudaError_t run_device(gbfft_plan p, const void* vin, void* vout, int64_t rows, cudaStream_t s) {
+    if (p->dtype == GBFFT_C2C_F64)
+        return launch_rows(*p->rv, p->direction, vin, vout, p->tw64, (long long)rows, 0, s, p->status);
+    const float2* in = (const float2*)vin;
+    float2* out = (float2*)vout;
     if (p->kind == kPlanTensorCore && p->umv)
         return launch_umma(*p->umv, p->tc_prec, p->direction, in, out, p->tw, p->umma_b, (long long)rows,
                            p->grid_cap, p->status, s);
@@ -378,10 +428,10 @@ gbfft_status gbfft_plan_create_twopass(gbfft_plan* out, int64_t n, int64_t batch
 gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_stream) {
     if (!p || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
     if (p->batch == 0) return GBFFT_OK;
-    const size_t bytes = sizeof(float2) * (size_t)p->n * (size_t)p->batch;
+    const size_t bytes = elem_bytes(p->dtype) * (size_t)p->n * (size_t)p->batch;
     gbfft_status st = check_io(in, out, bytes);
     if (st != GBFFT_OK) return st;
-    cudaError_t e = run_device(p, (const float2*)in, (float2*)out, p->batch, (cudaStream_t)cuda_stream);
+    cudaError_t e = run_device(p, in, out, p->batch, (cudaStream_t)cuda_stream);
     return e == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
@@ -391,7 +441,7 @@ gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_s
 gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_out, void* cuda_stream) {
     if (!p || !host_in || !host_out || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
     if (p->batch == 0) return GBFFT_OK;
-    const size_t row_bytes = sizeof(float2) * (size_t)p->n;
+    const size_t row_bytes = elem_bytes(p->dtype) * (size_t)p->n;
     const size_t bytes = row_bytes * (size_t)p->batch;
     if (host_in != host_out) {
         const uintptr_t a = (uintptr_t)host_in, b = (uintptr_t)host_out;

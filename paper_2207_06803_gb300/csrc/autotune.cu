@@ -3,7 +3,8 @@
 //
 // gbfft_autotune times every way this library can run one length - each
 // compiled single-pass variant (radix schedule x tile shape x kernel shape),
-// each Eq. 2 two-pass split N = K * M, each tensor-core engine - on scratch
+// each Eq. 2 two-pass split N = K * M, each tensor-core engine, each FP64
+// variant of a complex128 plan - on scratch
 // buffers of the requested batch, and records the fastest in an in-process
 // wisdom table keyed by (n, dtype, direction).  gbfft_plan_create consults the
 // table when no variant is forced.  Wisdom is saved to / loaded from a text
@@ -144,6 +145,9 @@ gbfft_status gbfft_autotune(int64_t n, int64_t batch, int direction, int dtype, 
         static const int64_t lens[] = {32, 48, 64, 80, 96, 112, 128, 256, 512};
         for (int64_t k : lens)
             if (n % k == 0 && cols_variant_for(k) && cols_variant_for(n / k)) cands.push_back({-1, k});
+    } else if (dtype == GBFFT_C2C_F64) {
+        const int nv = rows_variants_f64_for(n, nullptr, 0);
+        for (int v = 0; v < nv; ++v) cands.push_back({v, 0});
     } else if (dtype == GBFFT_C2C_F32_TC_FP16X2 || dtype == GBFFT_C2C_F32_TC_BF16X2) {
         cands.push_back({0, 0});
         cands.push_back({1, 0});
@@ -151,7 +155,7 @@ gbfft_status gbfft_autotune(int64_t n, int64_t batch, int direction, int dtype, 
         return GBFFT_ERR_INVALID_ARG;
     }
     if (cands.empty()) return GBFFT_ERR_UNSUPPORTED_SIZE;
-    const size_t bytes = sizeof(float2) * (size_t)n * (size_t)batch;
+    const size_t bytes = (dtype == GBFFT_C2C_F64 ? sizeof(double2) : sizeof(float2)) * (size_t)n * (size_t)batch;
     void *din = nullptr, *dout = nullptr;
     if (cudaMalloc(&din, bytes) != cudaSuccess || cudaMalloc(&dout, bytes) != cudaSuccess) {
         cudaGetLastError();

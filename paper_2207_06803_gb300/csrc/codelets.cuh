@@ -1,4 +1,5 @@
-// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16, 32, 64}, fully unrolled.
+// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16, 32, 64}, fully unrolled, on
+// float2 (FP32 path) or double2 (FP64 path) values.
 //
 // Each codelet computes A = DFT_r a in place on r complex values held in
 // registers, natural order in and out, with DFT_r[m][k] = w^(m*k) and
@@ -13,43 +14,71 @@
 
 namespace gbfft {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+// Complex values are C (FP32 path) or double2 (FP64 path); every helper
+// below exists for both, and the codelets are templates over the type.
+template <class C>
+struct RealOf;
+template <>
+struct RealOf<float2> {
+    using T = float;
+};
+template <>
+struct RealOf<double2> {
+    using T = double;
+};
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+template <class C>
+__device__ __forceinline__ C cadd(C a, C b) {
+    return C{a.x + b.x, a.y + b.y};
+}
+template <class C>
+__device__ __forceinline__ C csub(C a, C b) {
+    return C{a.x - b.x, a.y - b.y};
+}
+template <class C>
+__device__ __forceinline__ C cmul(C a, C b) {
+    return C{fmaT(a.x, b.x, -a.y * b.y), fmaT(a.x, b.y, a.y * b.x)};
 }
 // a * conj(b)
-__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+template <class C>
+__device__ __forceinline__ C cmulc(C a, C b) {
+    return C{fmaT(a.x, b.x, a.y * b.y), fmaT(a.y, b.x, -a.x * b.y)};
 }
 // a * (S * i)
-template <int S>
-__device__ __forceinline__ float2 mul_si(float2 a) {
-    return S > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+template <int S, class C>
+__device__ __forceinline__ C mul_si(C a) {
+    return S > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
 }
-// a * (c + i*S*s) for compile-time constants c, s
-template <int S>
-__device__ __forceinline__ float2 mul_const(float2 a, float c, float s) {
-    const float ss = S > 0 ? s : -s;
-    return make_float2(fmaf(a.x, c, -a.y * ss), fmaf(a.x, ss, a.y * c));
+// a * (c + i*S*s) for compile-time constants c, s (given in double precision
+// and rounded once to the working precision).
+template <int S, class C>
+__device__ __forceinline__ C mul_const(C a, double cd, double sd) {
+    using T = typename RealOf<C>::T;
+    const T c = (T)cd, s = (T)sd;
+    const T ss = S > 0 ? s : -s;
+    return C{fmaT(a.x, c, -a.y * ss), fmaT(a.x, ss, a.y * c)};
 }
 // Twiddle application for direction S from a forward-table entry w = exp(-2*pi*i*e/N).
-template <int S>
-__device__ __forceinline__ float2 twiddle(float2 a, float2 w) {
+template <int S, class C>
+__device__ __forceinline__ C twiddle(C a, C w) {
     return S < 0 ? cmul(a, w) : cmulc(a, w);
 }
 
-constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
-constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
-constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
+constexpr double kC8 = 0.70710678118654752440;   // cos(pi/4)
+constexpr double kC16 = 0.92387953251128675613;  // cos(pi/8)
+constexpr double kS16 = 0.38268343236508977173;  // sin(pi/8)
 
 template <int S, int R>
 struct Dft;
 
 template <int S>
 struct Dft<S, 2> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 t = a[0];
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        C t = a[0];
         a[0] = cadd(t, a[1]);
         a[1] = csub(t, a[1]);
     }
@@ -57,9 +86,10 @@ struct Dft<S, 2> {
 
 template <int S>
 struct Dft<S, 4> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
-        float2 t2 = cadd(a[1], a[3]), t3 = mul_si<S>(csub(a[1], a[3]));
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        C t0 = cadd(a[0], a[2]), t1 = csub(a[0], a[2]);
+        C t2 = cadd(a[1], a[3]), t3 = mul_si<S>(csub(a[1], a[3]));
         a[0] = cadd(t0, t2);
         a[2] = csub(t0, t2);
         a[1] = cadd(t1, t3);
@@ -70,9 +100,10 @@ struct Dft<S, 4> {
 // DFT_8: even/odd split (K = 2, M = 4 in Eq. 2).
 template <int S>
 struct Dft<S, 8> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 e[4] = {a[0], a[2], a[4], a[6]};
-        float2 o[4] = {a[1], a[3], a[5], a[7]};
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        C e[4] = {a[0], a[2], a[4], a[6]};
+        C o[4] = {a[1], a[3], a[5], a[7]};
         Dft<S, 4>::run(e);
         Dft<S, 4>::run(o);
         o[1] = mul_const<S>(o[1], kC8, kC8);    // w8^1
@@ -90,8 +121,9 @@ struct Dft<S, 8> {
 //   X[j1 + 4*j2] = sum_k w4^(j2*k) * w16^(j1*k) * sum_m w4^(j1*m) x[4m + k].
 template <int S>
 struct Dft<S, 16> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 z[4][4];
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        C z[4][4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
 #pragma unroll
@@ -110,7 +142,7 @@ struct Dft<S, 16> {
         z[3][3] = mul_const<S>(z[3][3], -kC16, -kS16);
 #pragma unroll
         for (int j1 = 0; j1 < 4; ++j1) {
-            float2 c[4] = {z[0][j1], z[1][j1], z[2][j1], z[3][j1]};
+            C c[4] = {z[0][j1], z[1][j1], z[2][j1], z[3][j1]};
             Dft<S, 4>::run(c);
 #pragma unroll
             for (int j2 = 0; j2 < 4; ++j2) a[j1 + 4 * j2] = c[j2];
@@ -119,33 +151,34 @@ struct Dft<S, 16> {
 };
 
 // cos(pi*j/16), j = 0..8 (sin(pi*j/16) = cos(pi*(8-j)/16)).
-__device__ __forceinline__ constexpr float cos_pi16(int j) {
-    return j == 0 ? 1.0f
-         : j == 1 ? 0.98078528040323044913f
-         : j == 2 ? 0.92387953251128675613f
-         : j == 3 ? 0.83146961230254523708f
-         : j == 4 ? 0.70710678118654752440f
-         : j == 5 ? 0.55557023301960222474f
-         : j == 6 ? 0.38268343236508977173f
-         : j == 7 ? 0.19509032201612826785f
-                  : 0.0f;
+__device__ __forceinline__ constexpr double cos_pi16(int j) {
+    return j == 0 ? 1.0
+         : j == 1 ? 0.98078528040323044913
+         : j == 2 ? 0.92387953251128675613
+         : j == 3 ? 0.83146961230254523708
+         : j == 4 ? 0.70710678118654752440
+         : j == 5 ? 0.55557023301960222474
+         : j == 6 ? 0.38268343236508977173
+         : j == 7 ? 0.19509032201612826785
+                  : 0.0;
 }
 
 // a * w32^j for j in 0..15, w32 = exp(S*2*pi*i/32) = (cos(pi j/16), S sin(pi j/16)).
-template <int S>
-__device__ __forceinline__ float2 mul_w32(float2 a, int j) {
+template <int S, class C>
+__device__ __forceinline__ C mul_w32(C a, int j) {
     if (j == 0) return a;
     if (j == 8) return mul_si<S>(a);
-    const float c = j < 8 ? cos_pi16(j) : -cos_pi16(16 - j);
-    const float s = j < 8 ? cos_pi16(8 - j) : cos_pi16(j - 8);
+    const double c = j < 8 ? cos_pi16(j) : -cos_pi16(16 - j);
+    const double s = j < 8 ? cos_pi16(8 - j) : cos_pi16(j - 8);
     return mul_const<S>(a, c, s);
 }
 
 // DFT_32: even/odd split (K = 2, M = 16 in Eq. 2).
 template <int S>
 struct Dft<S, 32> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 e[16], o[16];
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        C e[16], o[16];
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             e[m] = a[2 * m];
@@ -155,7 +188,7 @@ struct Dft<S, 32> {
         Dft<S, 16>::run(o);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            const float2 t = mul_w32<S>(o[k], k);
+            const C t = mul_w32<S>(o[k], k);
             a[k] = cadd(e[k], t);
             a[k + 16] = csub(e[k], t);
         }
@@ -163,36 +196,36 @@ struct Dft<S, 32> {
 };
 
 // cos(pi*j/32), j = 0..16.
-__device__ __forceinline__ constexpr float cos_pi32(int j) {
-    return j == 0 ? 1.0f
-         : j == 1 ? 0.99518472667219688624f
-         : j == 2 ? 0.98078528040323044913f
-         : j == 3 ? 0.95694033573220886494f
-         : j == 4 ? 0.92387953251128675613f
-         : j == 5 ? 0.88192126434835502971f
-         : j == 6 ? 0.83146961230254523708f
-         : j == 7 ? 0.77301045336273696081f
-         : j == 8 ? 0.70710678118654752440f
-         : j == 9 ? 0.63439328416364549822f
-         : j == 10 ? 0.55557023301960222474f
-         : j == 11 ? 0.47139673682599764856f
-         : j == 12 ? 0.38268343236508977173f
-         : j == 13 ? 0.29028467725446236764f
-         : j == 14 ? 0.19509032201612826785f
-         : j == 15 ? 0.09801714032956060199f
-                   : 0.0f;
+__device__ __forceinline__ constexpr double cos_pi32(int j) {
+    return j == 0 ? 1.0
+         : j == 1 ? 0.99518472667219688624
+         : j == 2 ? 0.98078528040323044913
+         : j == 3 ? 0.95694033573220886494
+         : j == 4 ? 0.92387953251128675613
+         : j == 5 ? 0.88192126434835502971
+         : j == 6 ? 0.83146961230254523708
+         : j == 7 ? 0.77301045336273696081
+         : j == 8 ? 0.70710678118654752440
+         : j == 9 ? 0.63439328416364549822
+         : j == 10 ? 0.55557023301960222474
+         : j == 11 ? 0.47139673682599764856
+         : j == 12 ? 0.38268343236508977173
+         : j == 13 ? 0.29028467725446236764
+         : j == 14 ? 0.19509032201612826785
+         : j == 15 ? 0.09801714032956060199
+                   : 0.0;
 }
 
 // a * w64^e for 0 <= e < 64, w64 = exp(S*2*pi*i/64) = (cos(pi e/32), S sin(pi e/32)),
 // with the angle reduced to the first octant by quadrant symmetry.
-template <int S>
-__device__ __forceinline__ float2 mul_w64(float2 a, int e) {
+template <int S, class C>
+__device__ __forceinline__ C mul_w64(C a, int e) {
     e &= 63;
     if (e == 0) return a;
     if (e == 16) return mul_si<S>(a);
-    if (e == 32) return make_float2(-a.x, -a.y);
+    if (e == 32) return C{-a.x, -a.y};
     if (e == 48) return mul_si<-S>(a);
-    float c, s;
+    double c, s;
     if (e < 16) {
         c = cos_pi32(e);
         s = cos_pi32(16 - e);
@@ -213,8 +246,9 @@ __device__ __forceinline__ float2 mul_w64(float2 a, int e) {
 //   X[j1 + 8*j2] = sum_k w8^(j2*k) * w64^(j1*k) * sum_m w8^(j1*m) x[8m + k].
 template <int S>
 struct Dft<S, 64> {
-    __device__ __forceinline__ static void run(float2* a) {
-        float2 z[8][8];
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        C z[8][8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
 #pragma unroll
@@ -225,7 +259,7 @@ struct Dft<S, 64> {
         }
 #pragma unroll
         for (int j1 = 0; j1 < 8; ++j1) {
-            float2 c[8];
+            C c[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) c[k] = z[k][j1];
             Dft<S, 8>::run(c);
@@ -242,58 +276,60 @@ template <int P>
 struct PrimeConsts;
 template <>
 struct PrimeConsts<3> {
-    __device__ __forceinline__ static float c(int j) { return -0.5f; }
-    __device__ __forceinline__ static float s(int j) { return 0.86602540378443864676f; }
+    __device__ __forceinline__ static double c(int j) { return -0.5; }
+    __device__ __forceinline__ static double s(int j) { return 0.86602540378443864676; }
 };
 template <>
 struct PrimeConsts<5> {
-    __device__ __forceinline__ static float c(int j) {
-        return j == 1 ? 0.30901699437494742410f : -0.80901699437494742410f;
+    __device__ __forceinline__ static double c(int j) {
+        return j == 1 ? 0.30901699437494742410 : -0.80901699437494742410;
     }
-    __device__ __forceinline__ static float s(int j) {
-        return j == 1 ? 0.95105651629515357212f : 0.58778525229247312917f;
+    __device__ __forceinline__ static double s(int j) {
+        return j == 1 ? 0.95105651629515357212 : 0.58778525229247312917;
     }
 };
 template <>
 struct PrimeConsts<7> {
-    __device__ __forceinline__ static float c(int j) {
-        return j == 1 ? 0.62348980185873353053f : (j == 2 ? -0.22252093395631440429f : -0.90096886790241912624f);
+    __device__ __forceinline__ static double c(int j) {
+        return j == 1 ? 0.62348980185873353053 : (j == 2 ? -0.22252093395631440429 : -0.90096886790241912624);
     }
-    __device__ __forceinline__ static float s(int j) {
-        return j == 1 ? 0.78183148246802980871f : (j == 2 ? 0.97492791218182360702f : 0.43388373911755812048f);
+    __device__ __forceinline__ static double s(int j) {
+        return j == 1 ? 0.78183148246802980871 : (j == 2 ? 0.97492791218182360702 : 0.43388373911755812048);
     }
 };
 
 template <int S, int P>
 struct DftPrime {
-    __device__ __forceinline__ static void run(float2* a) {
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
         constexpr int H = (P - 1) / 2;
-        float2 t[H + 1], u[H + 1];
+        C t[H + 1], u[H + 1];
 #pragma unroll
         for (int m = 1; m <= H; ++m) {
             t[m] = cadd(a[m], a[P - m]);
             u[m] = csub(a[m], a[P - m]);
         }
-        float2 a0 = a[0];
-        float2 sum = a0;
+        C a0 = a[0];
+        C sum = a0;
 #pragma unroll
         for (int m = 1; m <= H; ++m) sum = cadd(sum, t[m]);
 #pragma unroll
         for (int k = 1; k <= H; ++k) {
-            float2 pr = a0, qs = make_float2(0.f, 0.f);
+            C pr = a0, qs = C{};
 #pragma unroll
             for (int m = 1; m <= H; ++m) {
                 // (k*m mod P) folded onto 1..H: cos is even, sin is odd.
                 const int e = (k * m) % P;
                 const int f = e <= H ? e : P - e;
-                const float cs = PrimeConsts<P>::c(f);
-                const float sn = e <= H ? PrimeConsts<P>::s(f) : -PrimeConsts<P>::s(f);
-                pr.x = fmaf(cs, t[m].x, pr.x);
-                pr.y = fmaf(cs, t[m].y, pr.y);
-                qs.x = fmaf(sn, u[m].x, qs.x);
-                qs.y = fmaf(sn, u[m].y, qs.y);
+                using T = typename RealOf<C>::T;
+                const T cs = (T)PrimeConsts<P>::c(f);
+                const T sn = (T)(e <= H ? PrimeConsts<P>::s(f) : -PrimeConsts<P>::s(f));
+                pr.x = fmaT(cs, t[m].x, pr.x);
+                pr.y = fmaT(cs, t[m].y, pr.y);
+                qs.x = fmaT(sn, u[m].x, qs.x);
+                qs.y = fmaT(sn, u[m].y, qs.y);
             }
-            const float2 iq = mul_si<S>(qs);  // i*S*Q
+            const C iq = mul_si<S>(qs);  // i*S*Q
             a[k] = cadd(pr, iq);
             a[P - k] = csub(pr, iq);
         }

@@ -117,6 +117,9 @@ bool wisdom_lookup(int64_t n, int dtype, int direction, int* variant, int64_t* k
 // Per-translation-unit variant tables, gathered by the registry in api.cu.
 const RowsVariant* rows_variants_pow2(int* count);
 const RowsVariant* rows_variants_mixed(int* count);
+// Complex128 / FP64 single-pass variants (rows_f64.cu).
+const RowsVariant* rows_variants_f64(int* count);
+int rows_variants_f64_for(int64_t n, const RowsVariant** out, int max_out);
 
 // All variants for length n, in preference order (the first is the default).
 int rows_variants_for(int64_t n, const RowsVariant** out, int max_out);
@@ -132,7 +135,7 @@ cudaError_t prepare_rows(const RowsVariant& v);
 // grid of a persistent variant (see persistent_grid); ignored otherwise.
 // `status` receives bounded-wait timeouts of the TMA variants (may be null
 // for the others).
-cudaError_t launch_rows(const RowsVariant& v, int direction, const float2* in, float2* out, const float2* tw,
+cudaError_t launch_rows(const RowsVariant& v, int direction, const void* in, void* out, const void* tw,
                         long long batch, int grid_cap, cudaStream_t stream, int* status = nullptr);
 
 // tw[j] = exp(-2*pi*i*j/n) for j < n, evaluated in FP64 on the device.
@@ -141,5 +144,6 @@ cudaError_t launch_twiddle_table(float2* tw, int64_t n, cudaStream_t stream);
 // Stage twiddle blocks of a schedule (see stockham.cuh): entries and launch.
 int stage_twiddle_count(const int* radix, int nstages);
 cudaError_t launch_stage_twiddles(float2* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream);
+cudaError_t launch_stage_twiddles64(double2* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream);
 
 }  // namespace gbfft

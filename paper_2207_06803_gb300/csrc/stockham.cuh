@@ -70,23 +70,23 @@ struct StageTwiddles<L, R, Rest...> {
     static constexpr int value = (L > 1 ? (R - 1) * L : 0) + StageTwiddles<L * R, Rest...>::value;
 };
 
-// Row addressing of a tile: element n of tile row t.
-// ContigIO: rows are consecutive (row t at base + t*N).
-template <int N>
+// Row addressing of a tile: element n of tile row t, complex type C (float2
+// or double2).  ContigIO: rows are consecutive (row t at base + t*N).
+template <int N, class C = float2>
 struct ContigIO {
-    const float2* in;
-    float2* out;
-    __device__ __forceinline__ float2 ld(int t, int n) const { return in[t * N + n]; }
-    __device__ __forceinline__ void st(int t, int n, float2 v) const { out[t * N + n] = v; }
+    const C* in;
+    C* out;
+    __device__ __forceinline__ C ld(int t, int n) const { return in[t * N + n]; }
+    __device__ __forceinline__ void st(int t, int n, C v) const { out[t * N + n] = v; }
 };
-// IndexedIO: row t starts at complex element off[t] of both buffers (ragged batches).
-template <int N>
+// IndexedIO: row t starts at complex element off[t] of both buffers.
+template <int N, class C = float2>
 struct IndexedIO {
-    const float2* in;
-    float2* out;
+    const C* in;
+    C* out;
     const long long* off;
-    __device__ __forceinline__ float2 ld(int t, int n) const { return in[off[t] + n]; }
-    __device__ __forceinline__ void st(int t, int n, float2 v) const { out[off[t] + n] = v; }
+    __device__ __forceinline__ C ld(int t, int n) const { return in[off[t] + n]; }
+    __device__ __forceinline__ void st(int t, int n, C v) const { out[off[t] + n] = v; }
 };
 
 // Butterflies of radix R per thread when TPB threads share the T*N/R
@@ -97,8 +97,8 @@ constexpr int stage_nb() {
 }
 
 // Stage-1 operands of this thread's butterflies, straight from HBM.
-template <int N, int E, int T, int R, class IO, int TPB = T * N / E>
-__device__ __forceinline__ void gather_global(float2 (&v)[E], const IO& io, int nvalid) {
+template <int N, int E, int T, int R, class IO, int TPB = T * N / E, class C>
+__device__ __forceinline__ void gather_global(C (&v)[E], const IO& io, int nvalid) {
     constexpr int NB = stage_nb<N, T, TPB, R>(), NR = N / R, NBT = T * N / R;
     static_assert(NB * R <= E, "register capacity too small for this stage");
     const int tid = threadIdx.x;
@@ -108,13 +108,13 @@ __device__ __forceinline__ void gather_global(float2 (&v)[E], const IO& io, int 
         if (NBT % TPB != 0 && B >= NBT) break;
         const int t = B / NR, j = B % NR;
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[u * R + q] = (t < nvalid) ? io.ld(t, j + q * NR) : make_float2(0.f, 0.f);
+        for (int q = 0; q < R; ++q) v[u * R + q] = (t < nvalid) ? io.ld(t, j + q * NR) : C{};
     }
 }
 
 // Stage operands from the shared-memory tile.
-template <int N, int E, int T, int PS, int R, int TPB = T * N / E>
-__device__ __forceinline__ void gather_smem(float2 (&v)[E], const float2* sm) {
+template <int N, int E, int T, int PS, int R, int TPB = T * N / E, class C>
+__device__ __forceinline__ void gather_smem(C (&v)[E], const C* sm) {
     constexpr int NB = stage_nb<N, T, TPB, R>(), NR = N / R, NBT = T * N / R;
     static_assert(NB * R <= E, "register capacity too small for this stage");
     const int tid = threadIdx.x;
@@ -134,9 +134,10 @@ __device__ __forceinline__ void gather_smem(float2 (&v)[E], const float2* sm) {
 // The stage loop with an explicit thread count TPB: stage s runs
 // ceil(T*N/R_s / TPB) butterflies per thread (guarded when uneven), so a
 // schedule may mix radices whose butterfly counts do not divide the threads.
-template <int N, int S, int E, int T, int PS, int TPB, bool SYNC0, int TWO, int L, int R, int... Rest, class IO>
-__device__ __forceinline__ void run_stages_t(float2 (&v)[E], const IO& io, float2* sm,
-                                             const float2* __restrict__ tw, int nvalid) {
+template <int N, int S, int E, int T, int PS, int TPB, bool SYNC0, int TWO, int L, int R, int... Rest, class IO,
+          class C>
+__device__ __forceinline__ void run_stages_t(C (&v)[E], const IO& io, C* sm, const C* __restrict__ tw,
+                                             int nvalid) {
     constexpr int NB = stage_nb<N, T, TPB, R>();  // butterflies per thread in this stage
     constexpr int NR = N / R;                     // butterflies per row
     constexpr int NBT = T * N / R;                // butterflies in the tile
@@ -187,9 +188,8 @@ __device__ __forceinline__ void run_stages_t(float2 (&v)[E], const IO& io, float
 }
 
 // Stages with TPB = T*N/E threads (every stage's butterflies divide evenly).
-template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest, class IO>
-__device__ __forceinline__ void run_stages(float2 (&v)[E], const IO& io, float2* sm, const float2* __restrict__ tw,
-                                           int nvalid) {
+template <int N, int S, int E, int T, int PS, bool SYNC0, int TWO, int L, int R, int... Rest, class IO, class C>
+__device__ __forceinline__ void run_stages(C (&v)[E], const IO& io, C* sm, const C* __restrict__ tw, int nvalid) {
     run_stages_t<N, S, E, T, PS, T * N / E, SYNC0, TWO, L, R, Rest...>(v, io, sm, tw, nvalid);
 }
 
@@ -237,6 +237,20 @@ __global__ void __launch_bounds__(TPB) k_stockham_rows_t(const float2* in, float
     const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
     gather_global<N, E, T, First<Rs...>::value, ContigIO<N>, TPB>(v, io, nvalid);
     run_stages_t<N, S, E, T, PS, TPB, false, 0, 1, Rs...>(v, io, sm, tw, nvalid);
+}
+
+// The same on complex128 rows (FP64 arithmetic, double2 stage twiddles).
+template <int N, int S, int TPB, int T, int PS, int... Rs>
+__global__ void __launch_bounds__(TPB) k_stockham_rows_d(const double2* in, double2* out,
+                                                          const double2* __restrict__ tw, long long batch) {
+    constexpr int E = capacity_of_r<N, T, TPB, Rs...>();
+    extern __shared__ double2 smd[];
+    const long long tile = blockIdx.x;
+    const int nvalid = tile_rows(tile, T, batch);
+    double2 v[E];
+    const ContigIO<N, double2> io{in + tile * T * N, out + tile * T * N};
+    gather_global<N, E, T, First<Rs...>::value, ContigIO<N, double2>, TPB>(v, io, nvalid);
+    run_stages_t<N, S, E, T, PS, TPB, false, 0, 1, Rs...>(v, io, smd, tw, nvalid);
 }
 
 // Persistent form with register prefetch of the next tile's stage-1 operands.

@@ -19,13 +19,15 @@ __global__ void k_twiddle_table(float2* tw, long long n) {
 }
 
 // Stage blocks: for each stage s >= 2 of the schedule (L = R_1..R_{s-1} > 1),
-// entry (q-1)*L + k of its block is w_N^(q*k*N/(L*R)), q in [1, R), k < L.
+// entry (q-1)*L + k of its block is w_N^(q*k*N/(L*R)), q in [1, R), k < L;
+// rounded once to float2 (FP32 path) or stored as double2 (FP64 path).
 struct ScheduleArg {
     int nstages;
     int radix[kMaxStages];
 };
 
-__global__ void k_stage_twiddles(float2* tw, long long n, ScheduleArg sch, int total) {
+template <class C>
+__global__ void k_stage_twiddles(C* tw, long long n, ScheduleArg sch, int total) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
     int off = 0;
@@ -40,7 +42,10 @@ __global__ void k_stage_twiddles(float2* tw, long long n, ScheduleArg sch, int t
                 const long long e = (q * k * (n / (L * R))) % n;
                 double sn, cs;
                 sincospi(2.0 * (double)e / (double)n, &sn, &cs);
-                tw[idx] = make_float2((float)cs, (float)(-sn));
+                if constexpr (sizeof(C) == sizeof(float2))
+                    tw[idx] = C{(float)cs, (float)(-sn)};
+                else
+                    tw[idx] = C{cs, -sn};
                 return;
             }
             off += sz;
@@ -59,15 +64,24 @@ int stage_twiddle_count(const int* radix, int nstages) {
     return total;
 }
 
-cudaError_t launch_stage_twiddles(float2* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream) {
+template <class C>
+static cudaError_t stage_twiddles(C* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream) {
     ScheduleArg sch{};
     sch.nstages = nstages;
     for (int s = 0; s < nstages && s < kMaxStages; ++s) sch.radix[s] = radix[s];
     const int total = stage_twiddle_count(radix, nstages);
     if (total == 0) return cudaSuccess;
     const int tpb = 256;
-    k_stage_twiddles<<<(total + tpb - 1) / tpb, tpb, 0, stream>>>(tw, (long long)n, sch, total);
+    k_stage_twiddles<C><<<(total + tpb - 1) / tpb, tpb, 0, stream>>>(tw, (long long)n, sch, total);
     return cudaGetLastError();
+}
+
+cudaError_t launch_stage_twiddles(float2* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream) {
+    return stage_twiddles(tw, n, radix, nstages, stream);
+}
+
+cudaError_t launch_stage_twiddles64(double2* tw, int64_t n, const int* radix, int nstages, cudaStream_t stream) {
+    return stage_twiddles(tw, n, radix, nstages, stream);
 }
 
 __global__ void k_post_twiddles(float2* post, long long n, long long m) {

@@ -55,6 +55,23 @@ inline RowsVariant make_rows_t_variant() {
                        (const void*)&k_stockham_rows_t<N, +1, TPB, T, PS, Rs...>};
 }
 
+// Complex128 rows (FP64): like make_rows_t_variant with 16-byte elements.
+template <int N, int TPB, int T, int PS, int... Rs>
+inline RowsVariant make_rows_d_variant() {
+    static_assert(((Rs * ...) == N), "radix schedule must multiply to N");
+    return RowsVariant{kRowsDirect,
+                       N,
+                       capacity_of_r<N, T, TPB, Rs...>(),
+                       T,
+                       TPB,
+                       PS,
+                       (int)sizeof...(Rs),
+                       {Rs...},
+                       (int)(sizeof...(Rs) > 1 ? smem_elems<T, N, PS>() * sizeof(double2) : 0),
+                       (const void*)&k_stockham_rows_d<N, -1, TPB, T, PS, Rs...>,
+                       (const void*)&k_stockham_rows_d<N, +1, TPB, T, PS, Rs...>};
+}
+
 template <int N, int TPB, int T, int PS, int... Rs>
 inline RowsVariant make_rows_tma_variant() {
     static_assert(((Rs * ...) == N), "radix schedule must multiply to N");

@@ -24,6 +24,7 @@ GBFFT_INVERSE = +1
 GBFFT_C2C_F32 = 0
 GBFFT_C2C_F32_TC_FP16X2 = 1
 GBFFT_C2C_F32_TC_BF16X2 = 2
+GBFFT_C2C_F64 = 3
 
 STATUS_NAMES = {
     0: "GBFFT_OK",
