@@ -556,7 +556,8 @@ def run_f64(args):
     d_rt = torch.empty_like(d_in)
     stream = torch.cuda.current_stream()
     rows = {}
-    for n in [1 << k for k in range(3, 13)] + [1536, 2560, 3584]:
+    sizes = [int(v) for v in args.sizes.split(",")] if args.sizes else [1 << k for k in range(3, 13)] + [1536, 2560, 3584]
+    for n in sizes:
         batch = total // n
         res = {}
         for direction, name in ((-1, "fwd"), (1, "inv")):
