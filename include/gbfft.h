@@ -82,19 +82,23 @@ int gbfft_version(void);
  * INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.  *out is set to NULL on error.
  *
  * Tensor-core dtypes (GBFFT_C2C_F32_TC_*): n must be 16, 256 or 4096 (an
- * all-radix-16 schedule; BF16x2 only 256 and 4096, because its single-stage
- * error at 16, about 5e-6 relative L2, exceeds the 1e-6*log2(N) accuracy
- * contract of the tensor-core path).  Each stage's DFT_16 - the dense DFT(16) block of
- * the factorisation (Table I), multiplied as a matrix - runs as a 32x32 real
- * product on the tensor cores with both operands split into high and low
- * half-precision parts (Mh Xh + Mh Xl + Ml Xh, FP32 accumulation); FP16
- * columns are scaled by exact powers of two first.  Stage twiddles stay FP32.
- * gbfft_plan_create_variant with a tensor-core dtype selects the engine:
- * variant 1 (N = 256, 4096; the default there) issues tcgen05.mma from
- * shared-memory operands into tensor memory and reads results back with
- * tcgen05.ld; variant 0 (the default for N = 16) issues warp-level
- * mma.sync.m16n8k16 on register fragments.  The two-pass form is FP32-only
- * (INVALID_ARG otherwise).
+ * all-radix-16 schedule) or, FP16x2 only, a multiple of 8 up to 64 (the
+ * direct DFT below); BF16x2 only 256 and 4096, because its error in a single
+ * dense product, 4-6e-6 relative L2, exceeds the 1e-6*log2(N) accuracy
+ * contract of the tensor-core path at smaller N.  Each stage's DFT_16 - the
+ * dense DFT(16) block of the factorisation (Table I), multiplied as a matrix -
+ * runs as a 32x32 real product on the tensor cores with both operands split
+ * into high and low half-precision parts (Mh Xh + Mh Xl + Ml Xh, FP32
+ * accumulation); FP16 columns are scaled by exact powers of two first.  Stage
+ * twiddles stay FP32.  gbfft_plan_create_variant with a tensor-core dtype
+ * selects the engine: variant 1 (N = 256, 4096; the default there) issues
+ * tcgen05.mma from shared-memory operands into tensor memory and reads results
+ * back with tcgen05.ld; variant 0 (the default for N = 16) issues warp-level
+ * mma.sync.m16n8k16 on register fragments; variant 2 (N = 8, 16, 24, ..., 64;
+ * the default except at 16) is the direct DFT: y = F_N x as ONE split-precision
+ * real product [yr yi] = [xr xi] [[Fr, Fi], [-Fi, Fr]] per 128 transforms on
+ * tcgen05 (M = 128, K = N_out = 2N), no factorisation (the paper's direct-DFT
+ * variant, Sec. VI).  The two-pass form is FP32-only (INVALID_ARG otherwise).
  */
 gbfft_status gbfft_plan_create(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype);
 

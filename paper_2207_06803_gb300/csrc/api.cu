@@ -85,6 +85,8 @@ struct gbfft_plan_s {
     // tensor-core split precision (all-radix-16 schedule)
     const TcVariant* tcv = nullptr;
     const UmmaVariant* umv = nullptr;  // tcgen05 engine (variant 1) instead of mma.sync (variant 0)
+    const DirectVariant* dv = nullptr;  // direct DFT on tcgen05 (variant 2)
+    uint16_t* direct_b = nullptr;
     int tc_prec = 0;
     uint32_t* tc_frag = nullptr;
     uint16_t* umma_b = nullptr;
@@ -134,6 +136,7 @@ void free_plan(gbfft_plan p) {
     if (p->tc_frag) cudaFree(p->tc_frag);
     if (p->umma_b) cudaFree(p->umma_b);
     if (p->tw64) cudaFree(p->tw64);
+    if (p->direct_b) cudaFree(p->direct_b);
     float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
     for (float2* b : bufs)
         if (b) cudaFree(b);
@@ -173,7 +176,46 @@ gbfft_status alloc_stage_tables(float2** dst, int64_t n, const int* radix, int n
     return launch_stage_twiddles(*dst, n, radix, nstages, 0) == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
+// Direct DFT (variant 2 of the tensor-core dtypes): one split-precision matrix
+// product per 128 transforms, N a multiple of 8 up to 64.
+gbfft_status create_direct(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype) {
+    const DirectVariant* dv = direct_variant_for(n);
+    if (!dv) return GBFFT_ERR_NOT_FOUND;
+    // BF16x2 keeps ~16 significand bits: one dense product errs by 4-6e-6 relative
+    // L2 at every N, above the 1e-6*log2(N) contract for N <= 64.
+    if (dtype == GBFFT_C2C_F32_TC_BF16X2) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    gbfft_plan p = new (std::nothrow) gbfft_plan_s();
+    if (!p) return GBFFT_ERR_OOM;
+    p->kind = kPlanTensorCore;
+    p->n = n;
+    p->batch = batch;
+    p->direction = direction;
+    p->dtype = dtype;
+    p->dv = dv;
+    p->variant = 2;
+    p->tc_prec = dtype == GBFFT_C2C_F32_TC_FP16X2 ? 0 : 1;
+    gbfft_status st = GBFFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&p->direct_b, (size_t)dv->bmat_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        st = GBFFT_ERR_OOM;
+    }
+    if (st == GBFFT_OK && prepare_direct(*dv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && (p->grid_cap = direct_grid(*dv)) <= 0) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && launch_direct_bmat(p->direct_b, (int)n, p->tc_prec, direction, 0) != cudaSuccess)
+        st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st != GBFFT_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return GBFFT_OK;
+}
+
 gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int engine) {
+    if (engine == 2) return create_direct(out, n, batch, direction, dtype);
     const TcVariant* tv = tc_variant_for(n);
     if (!tv) return GBFFT_ERR_UNSUPPORTED_SIZE;
     const UmmaVariant* uv = engine == 1 ? umma_variant_for(n) : nullptr;
@@ -280,7 +322,7 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
             } else if (wv >= 0) {
                 const int limit = dtype == GBFFT_C2C_F32   ? rows_variants_for(n, nullptr, 0)
                                   : dtype == GBFFT_C2C_F64 ? rows_variants_f64_for(n, nullptr, 0)
-                                                           : 2;
+                                                           : 3;
                 if (wv < limit) variant = wv;
             }
         }
@@ -288,9 +330,11 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     if (dtype == GBFFT_C2C_F64) return create_f64(out, n, batch, direction, variant, k_outer);
     if (dtype != GBFFT_C2C_F32) {
         if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
-        if (variant > 1) return GBFFT_ERR_NOT_FOUND;
-        // default engine: tcgen05 where it exists (N = 256, 4096), else mma.sync
-        const int engine = variant >= 0 ? variant : (umma_variant_for(n) ? 1 : 0);
+        if (variant > 2) return GBFFT_ERR_NOT_FOUND;
+        // default engine: tcgen05 Stockham where it exists (N = 256, 4096), else mma.sync
+        // Stockham (N = 16), else the direct DFT (N = 8, 24, ..., 64)
+        const int engine = variant >= 0 ? variant
+                                        : (umma_variant_for(n) ? 1 : (tc_variant_for(n) ? 0 : (direct_variant_for(n) ? 2 : 0)));
         return create_tc(out, n, batch, direction, dtype, engine);
     }
 
@@ -364,6 +408,9 @@ cudaError_t run_device(gbfft_plan p, const void* vin, void* vout, int64_t rows, 
         return launch_rows(*p->rv, p->direction, vin, vout, p->tw64, (long long)rows, 0, s, p->status);
     const float2* in = (const float2*)vin;
     float2* out = (float2*)vout;
+    if (p->kind == kPlanTensorCore && p->dv)
+        return launch_direct(*p->dv, p->tc_prec, p->direction, in, out, p->direct_b, (long long)rows, p->grid_cap,
+                             p->status, s);
     if (p->kind == kPlanTensorCore && p->umv)
         return launch_umma(*p->umv, p->tc_prec, p->direction, in, out, p->tw, p->umma_b, (long long)rows,
                            p->grid_cap, p->status, s);
@@ -513,6 +560,8 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     int rad[2 * kMaxStages];
     if (p->kind == kPlanRagged) {
         // no single schedule: one per length class
+    } else if (p->kind == kPlanTensorCore && p->dv) {
+        rad[ns++] = (int)p->n;  // the direct DFT: one dense stage of radix N
     } else if (p->kind == kPlanTensorCore) {
         for (int i = 0; i < p->tcv->nstages; ++i) rad[ns++] = 16;
     } else if (p->kind == kPlanSingle) {
@@ -524,7 +573,7 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     if (nstages) *nstages = ns < kMaxStages ? ns : kMaxStages;
     if (radices)
         for (int i = 0; i < ns && i < kMaxStages; ++i) radices[i] = rad[i];
-    if (variant) *variant = p->kind == kPlanSingle ? p->variant : (p->kind == kPlanTensorCore ? (p->umv ? 1 : 0) : -1);
+    if (variant) *variant = p->kind == kPlanSingle ? p->variant : (p->kind == kPlanTensorCore ? (p->dv ? 2 : (p->umv ? 1 : 0)) : -1);
     if (workspace_bytes) *workspace_bytes = p->ws_bytes;
     return GBFFT_OK;
 }

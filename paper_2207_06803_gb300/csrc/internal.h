@@ -90,6 +90,19 @@ cudaError_t launch_umma(const UmmaVariant& v, int prec, int direction, const flo
                         const float2* tw, const void* bmat, long long batch, int grid_cap, int* status,
                         cudaStream_t s);
 
+// Direct DFT on tcgen05 for small N (direct.cu): y = F_N x as one split
+// half-precision matrix product per 128 transforms; N = 8, 16, ..., 64.
+struct DirectVariant {
+    int n, rows, tpb, smem, bmat_bytes, tmem_cols;
+    const void* k[2][2];  // [prec][dir]
+};
+const DirectVariant* direct_variant_for(int64_t n);
+cudaError_t prepare_direct(const DirectVariant& v);
+int direct_grid(const DirectVariant& v);
+cudaError_t launch_direct_bmat(uint16_t* bm, int n, int prec, int sign, cudaStream_t s);
+cudaError_t launch_direct(const DirectVariant& v, int prec, int direction, const float2* in, float2* out,
+                          const void* bmat, long long batch, int grid_cap, int* status, cudaStream_t s);
+
 // Ragged-batch plans (ragged.cu).
 struct RaggedState;
 gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* offsets, int64_t count);

@@ -31,6 +31,7 @@
 
 #include "internal.h"
 #include "stockham.cuh"
+#include "tcgen05.cuh"
 
 namespace gbfft {
 namespace {
@@ -45,90 +46,16 @@ __device__ __forceinline__ uint32_t a_offset(int row, int kgroup) {
     return (uint32_t)((row >> 3) * kSbo + kgroup * kLbo + (row & 7) * 16);
 }
 
-// Shared-memory matrix descriptor (tcgen05): start >> 4 [0,14), leading byte
-// offset >> 4 [16,30), stride byte offset >> 4 [32,46), fixed version 1
-// [46,48), base offset 0, no swizzle (layout type 0 in [61,64)).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((kLbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((kSbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) { return tc_smem_desc(saddr, kLbo, kSbo); }
 
-// Instruction descriptor, kind::f16: FP32 accumulator [4,6) = 1, A/B format
-// [7,10) / [10,13) (0 = F16, 1 = BF16), both K-major, N >> 3 at [17,23),
-// M >> 4 at [24,29).
-__host__ __device__ constexpr uint32_t instr_desc(int prec, int m, int n) {
-    return (1u << 4) | ((uint32_t)prec << 7) | ((uint32_t)prec << 10) | ((uint32_t)(n >> 3) << 17) |
-           ((uint32_t)(m >> 4) << 24);
-}
+__host__ __device__ constexpr uint32_t instr_desc(int prec, int m, int n) { return tc_instr_desc(prec, m, n); }
 
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "setp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-        "}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
+    tc_mma_f16(tmem_d, adesc, bdesc, idesc, accumulate);
 }
 
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 32 columns of 32-bit values starting at column `col` of this
-// warp's TMEM sub-partition; thread i gets lane i.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
-        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-template <int PREC>
-__device__ __forceinline__ uint32_t pack_hi(float a, float b, float& ra, float& rb) {
-    if constexpr (PREC == 0) {
-        const __half2 h = __floats2half2_rn(a, b);
-        const float2 f = __half22float2(h);
-        ra = a - f.x;
-        rb = b - f.y;
-        return *reinterpret_cast<const uint32_t*>(&h);
-    } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        const float2 f = __bfloat1622float2(h);
-        ra = a - f.x;
-        rb = b - f.y;
-        return *reinterpret_cast<const uint32_t*>(&h);
-    }
-}
-
-template <int PREC>
-__device__ __forceinline__ uint32_t pack_lo(float a, float b) {
-    if constexpr (PREC == 0) {
-        const __half2 h = __floats2half2_rn(a, b);
-        return *reinterpret_cast<const uint32_t*>(&h);
-    } else {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-        return *reinterpret_cast<const uint32_t*>(&h);
-    }
-}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) { tc_commit(bar); }
 
 struct UmmaShared {
     uint8_t* a_hi;       // MT tiles of 128 x 32

@@ -71,12 +71,15 @@ def test_tensor_core_config_sizes_sampled(n, batch, dtype):
 
 def test_tensor_core_rejects_other_sizes_and_forms():
     from paper_2207_06803_gb300 import gbfft
-    for n in (8, 512, 1024, 8192):
+    for n in (12, 72, 128, 512, 1024, 8192):
         with pytest.raises(gbfft.GbfftError) as e:
             gbfft.gbfft_plan_create(n, 4, -1, 1)
         assert e.value.status == gbfft.GBFFT_ERR_UNSUPPORTED_SIZE
     with pytest.raises(gbfft.GbfftError) as e:
-        gbfft.gbfft_plan_create_variant(256, 4, -1, 1, 2)  # engines are 0 (mma.sync) and 1 (tcgen05)
+        gbfft.gbfft_plan_create_variant(256, 4, -1, 1, 2)  # the direct DFT stops at N = 64
+    assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
+    with pytest.raises(gbfft.GbfftError) as e:
+        gbfft.gbfft_plan_create_variant(64, 4, -1, 1, 3)  # engines are 0, 1 and 2
     assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
     with pytest.raises(gbfft.GbfftError) as e:
         gbfft.gbfft_plan_create_variant(16, 4, -1, 1, 1)  # no tcgen05 engine at N = 16
@@ -134,3 +137,51 @@ def test_tcgen05_engine_matches_gate_and_mma_sync(n, batch, direction, dtype):
     err1 = row_rel_l2(outs[0], ref)
     assert np.all(np.isfinite(err1)) and err1.max() <= gate, err1.max()
     assert row_rel_l2(outs[0], outs[1].astype(np.complex128)).max() <= gate
+
+
+DIRECT_SIZES = (8, 16, 24, 32, 40, 48, 56, 64)
+
+
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_direct_dft_engine_every_size(direction):
+    """Direct DFT on tcgen05 (variant 2, FP16x2): every N, uniform and scaled
+    Gaussian rows (per-row dynamic range 10^+-3), a ragged last tile and
+    persistent CTAs walking several tiles, against the oracle."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    for n in DIRECT_SIZES:
+        for dist in ("uniform", "gaussian"):
+            batch = 128 * 700 + 37  # more tiles than resident CTAs, ragged tail
+            x = (synth.uniform_batch(SEED + n, n, batch) if dist == "uniform"
+                 else synth.gaussian_scaled_batch(SEED + n, n, batch))
+            d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+            d_out = torch.full_like(d_in, float("nan"))
+            with gbfft.Plan(n, batch, direction, dtype=1, variant=2) as p:
+                p.execute(d_in, d_out)
+                torch.cuda.synchronize()
+                assert gbfft.gbfft_plan_device_status(p.handle) == 0
+            rows = np.concatenate([synth.sample_rows(SEED, batch, 512), np.arange(batch - 40, batch)])
+            y = d_out.view(batch, 2 * n)[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.complex64)
+            ref = oracle.dft(x[rows].astype(np.complex128), direction, nthreads=ncpu())
+            err = row_rel_l2(y, ref)
+            assert np.all(np.isfinite(err)), (n, dist)
+            assert err.max() <= 1e-6 * math.log2(n), (n, dist, err.max())
+
+
+def test_direct_dft_in_place_default_engine_and_bf16_rejected():
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    n, batch = 48, 1000
+    x = synth.uniform_batch(SEED, n, batch)
+    d = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+    ref = torch.empty_like(d)
+    with gbfft.Plan(n, batch, -1, dtype=1) as p:  # default engine at N = 48: the direct DFT
+        assert p.info()["variant"] == 2
+        p.execute(d, ref)
+        p.execute(d, d)
+    torch.cuda.synchronize()
+    assert torch.equal(d, ref)
+    for n in DIRECT_SIZES:
+        with pytest.raises(gbfft.GbfftError) as e:
+            gbfft.gbfft_plan_create_variant(n, 4, -1, 2, 2)
+        assert e.value.status == gbfft.GBFFT_ERR_UNSUPPORTED_SIZE
