@@ -592,7 +592,8 @@ def run_tc(args, dists=("uniform", "gaussian_scaled")):
     stream = torch.cuda.current_stream()
     peak, src = _peak()
     out = {}
-    for n, dist in [(n, d) for d in dists for n in (256, 4096)]:
+    stockham_sizes = [] if getattr(args, "sizes", None) else [256, 4096]
+    for n, dist in [(n, d) for d in dists for n in stockham_sizes]:
         batch = TOTAL // n
         x = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL) if dist == "uniform" else \
             synth.gaussian_scaled_batch(synth.DEFAULT_SEED, n, batch).reshape(-1)
@@ -609,6 +610,27 @@ def run_tc(args, dists=("uniform", "gaussian_scaled")):
             rr = d_rt.view(batch, 2 * n)[:4096].double()
             rt = (torch.linalg.vector_norm(rr - n * xr, dim=1) / torch.linalg.vector_norm(n * xr, dim=1)).max()
             gbs = BYTES_PER_CALL / (ms * 1e-3) / 1e9
+            out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak,
+                                         "roundtrip_rel_l2_max": float(rt)}
+    # the direct DFT (one split-FP16 matrix product per 128 transforms) for small N
+    direct_sizes = [int(v) for v in args.sizes.split(",")] if getattr(args, "sizes", None) else \
+        [8, 16, 24, 32, 40, 48, 56, 64]
+    for n, dist in [(n, d) for d in dists for n in direct_sizes]:
+        batch = TOTAL // n
+        x = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL) if dist == "uniform" else \
+            synth.gaussian_scaled_batch(synth.DEFAULT_SEED, n, batch).reshape(-1)
+        d_in = torch.from_numpy(x[: batch * n].view(np.float32)).cuda()
+        d_out = torch.empty_like(d_in)
+        d_rt = torch.empty_like(d_in)
+        for name, dt, var in (("fp32", 0, None), ("fp16x2_direct", 1, 2)):
+            with gbfft.Plan(n, batch, -1, dt, variant=var) as pf, gbfft.Plan(n, batch, 1, dt, variant=var) as pi:
+                ms = _time_ms(torch, lambda: pf.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+                pi.execute(d_out, d_rt, stream)
+                torch.cuda.synchronize()
+            xr = d_in.view(batch, 2 * n)[:4096].double()
+            rr = d_rt.view(batch, 2 * n)[:4096].double()
+            rt = (torch.linalg.vector_norm(rr - n * xr, dim=1) / torch.linalg.vector_norm(n * xr, dim=1)).max()
+            gbs = 16.0 * n * batch / (ms * 1e-3) / 1e9
             out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak,
                                          "roundtrip_rel_l2_max": float(rt)}
     for key in list(out):

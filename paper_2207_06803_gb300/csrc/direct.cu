@@ -11,7 +11,8 @@
 // operands are first scaled by an exact power of two per transform.  No
 // factorisation is needed, so every N that is a multiple of 8 up to 64 works.
 //
-// Per tile: threads load the 128 rows with coalesced 16-byte loads (8 complex
+// Per tile (128, 256 or 512 transforms: one to four M = 128 blocks, one thread
+// per transform): threads load the rows with coalesced 16-byte loads (8 complex
 // per chunk), split them into the K-major A operands in shared memory, one
 // thread issues the MMAs and commits them to an mbarrier (bounded wait), each
 // warp reads its 32 rows of D back from tensor memory, and the rows leave
@@ -31,7 +32,7 @@ namespace gbfft {
 namespace {
 
 constexpr unsigned long long kDirectWaitNs = 1000000000ull;
-constexpr int kDirectRows = 128;  // transforms per tile (the MMA's M)
+constexpr int kDirectRows = 128;  // transforms per MMA block (the MMA's M)
 
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -39,16 +40,18 @@ constexpr uint32_t tmem_cols_for(int k) { return k <= 32 ? 32u : (k <= 64 ? 64u 
 
 template <int N>
 struct DirectGeom {
-    static constexpr int K = 2 * N;                      // [re parts | im parts]
-    static constexpr int LBO = 128;                      // K-adjacent core matrices
-    static constexpr int SBO = 16 * K;                   // 8-row groups: K/8 core matrices of 128 B
-    static constexpr int A_BYTES = kDirectRows * K * 2;  // one operand (hi or lo), halves
-    static constexpr int B_BYTES = 2 * K * K * 2;        // [Bh; Bl]: 2K rows of K halves
-    static constexpr int PITCH = 8 * N + 16;             // staging row pitch (bytes), conflict-free stores
-    static constexpr int AREG = round_up(cmax(2 * A_BYTES, kDirectRows * PITCH), 1024);
-    static constexpr int SMEM = AREG + B_BYTES + kDirectRows * 4 + 16;
-    static constexpr uint32_t COLS = tmem_cols_for(K);
-    static_assert(N % 8 == 0 && K <= 256, "direct DFT: N a multiple of 8, 2N <= 256");
+    static constexpr int BLK = N <= 16 ? 4 : (N <= 32 ? 2 : 1);  // 128-row blocks per tile (M = 128 MMAs)
+    static constexpr int ROWS = kDirectRows * BLK;               // transforms per tile = threads per CTA
+    static constexpr int K = 2 * N;                              // [re parts | im parts]
+    static constexpr int LBO = 128;                              // K-adjacent core matrices
+    static constexpr int SBO = 16 * K;                           // 8-row groups: K/8 core matrices of 128 B
+    static constexpr int A_BYTES = kDirectRows * K * 2;          // one block's operand (hi or lo), halves
+    static constexpr int B_BYTES = 2 * K * K * 2;                // [Bh; Bl]: 2K rows of K halves
+    static constexpr int PITCH = 8 * N + 16;                     // staging row pitch (bytes), conflict-free
+    static constexpr int AREG = round_up(cmax(2 * BLK * A_BYTES, ROWS * PITCH), 1024);
+    static constexpr int SMEM = AREG + B_BYTES + ROWS * 4 + 16;
+    static constexpr uint32_t COLS = tmem_cols_for(BLK * K);
+    static_assert(N % 8 == 0 && BLK * K <= 256, "direct DFT: N a multiple of 8, tile columns <= 256");
 };
 
 __device__ __forceinline__ uint32_t k_offset(int row, int kg, int sbo) {
@@ -56,23 +59,23 @@ __device__ __forceinline__ uint32_t k_offset(int row, int kg, int sbo) {
 }
 
 template <int N, int S, int PREC>
-__global__ void __launch_bounds__(kDirectRows) k_dft_direct_umma(const float2* in, float2* out,
-                                                                 const uint4* __restrict__ bmat, long long batch,
-                                                                 int* status) {
+__global__ void __launch_bounds__(DirectGeom<N>::ROWS) k_dft_direct_umma(const float2* in, float2* out,
+                                                                         const uint4* __restrict__ bmat,
+                                                                         long long batch, int* status) {
     using Geo = DirectGeom<N>;
-    constexpr int K = DirectGeom<N>::K, CPR = N / 8;  // 8-complex chunks per row
+    constexpr int K = Geo::K, BLK = Geo::BLK, ROWS = Geo::ROWS, CPR = N / 8;  // 8-complex chunks per row
     constexpr int G = CPR <= 1 ? 1 : (CPR <= 2 ? 2 : (CPR <= 4 ? 4 : 8));
     extern __shared__ __align__(1024) uint8_t dsm[];
-    uint8_t* const a_hi = dsm;
-    uint8_t* const a_lo = dsm + Geo::A_BYTES;
+    uint8_t* const a_hi = dsm;                         // BLK blocks of 128 x K halves
+    uint8_t* const a_lo = dsm + BLK * Geo::A_BYTES;
     uint8_t* const stage = dsm;  // output staging reuses the A region once the MMAs are done
     uint8_t* const bsm = dsm + Geo::AREG;
     int* const s_exp = reinterpret_cast<int*>(bsm + Geo::B_BYTES);
-    uint64_t* const bar = reinterpret_cast<uint64_t*>(s_exp + kDirectRows);
+    uint64_t* const bar = reinterpret_cast<uint64_t*>(s_exp + ROWS);
     uint32_t* const tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
     const int tid = threadIdx.x;
 
-    for (int i = tid; i < Geo::B_BYTES / 16; i += kDirectRows) reinterpret_cast<uint4*>(bsm)[i] = bmat[i];
+    for (int i = tid; i < Geo::B_BYTES / 16; i += ROWS) reinterpret_cast<uint4*>(bsm)[i] = bmat[i];
     if (tid == 0) {
         mbar_init(bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -89,18 +92,18 @@ __global__ void __launch_bounds__(kDirectRows) k_dft_direct_umma(const float2* i
     const uint32_t tmem = *tmem_slot;
     uint32_t phase = 0;
     bool ok = true;
-    const long long ntiles = (batch + kDirectRows - 1) / kDirectRows;
+    const long long ntiles = (batch + ROWS - 1) / ROWS;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();  // the previous tile's staging reads are done
-        const long long r0 = tile * kDirectRows;
-        const int nvalid = (int)min((long long)kDirectRows, batch - r0);
+        const long long r0 = tile * ROWS;
+        const int nvalid = (int)min((long long)ROWS, batch - r0);
         const float4* src = reinterpret_cast<const float4*>(in + r0 * N);
         // Load, scale and split.  Each row is served by G lanes (G = CPR rounded up
         // to a power of two, so that a row's lanes form an aligned group for the
         // shuffle reduction); lane j < CPR of the group holds complex 8j..8j+7.
 #pragma unroll
         for (int it = 0; it < G; ++it) {
-            const int row = it * (kDirectRows / G) + tid / G, j = tid % G;
+            const int row = it * (ROWS / G) + tid / G, j = tid % G;
             const bool have = j < CPR;
             float re[8], im[8];
 #pragma unroll
@@ -140,7 +143,9 @@ __global__ void __launch_bounds__(kDirectRows) k_dft_direct_umma(const float2* i
                     hi_[p] = pack_hi<PREC>(im[2 * p], im[2 * p + 1], a, b);
                     li[p] = pack_lo<PREC>(a, b);
                 }
-                const uint32_t o_re = k_offset(row, j, Geo::SBO), o_im = k_offset(row, N / 8 + j, Geo::SBO);
+                const uint32_t blk = (uint32_t)(row / kDirectRows) * Geo::A_BYTES;
+                const int rr = row % kDirectRows;
+                const uint32_t o_re = blk + k_offset(rr, j, Geo::SBO), o_im = blk + k_offset(rr, N / 8 + j, Geo::SBO);
                 *reinterpret_cast<uint4*>(a_hi + o_re) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
                 *reinterpret_cast<uint4*>(a_lo + o_re) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
                 *reinterpret_cast<uint4*>(a_hi + o_im) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
@@ -154,30 +159,34 @@ __global__ void __launch_bounds__(kDirectRows) k_dft_direct_umma(const float2* i
         if (tid == 0) {
             const uint32_t idesc = tc_instr_desc(PREC, kDirectRows, K);
             const uint32_t bh = smem_u32(bsm), bl = bh + (uint32_t)(K / 8) * Geo::SBO;  // rows K..2K-1 = Bl
-            const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
-            // D = Al Bh^T + Ah Bl^T + Ah Bh^T (small terms first), K = 16 per instruction
 #pragma unroll
-            for (int ks = 0; ks < K / 16; ++ks)
-                tc_mma_f16(tmem, tc_smem_desc(al + ks * 256, Geo::LBO, Geo::SBO), tc_smem_desc(bh + ks * 256, Geo::LBO, Geo::SBO),
-                           idesc, ks);
+            for (int b = 0; b < BLK; ++b) {
+                const uint32_t d = tmem + (uint32_t)(b * K);
+                const uint32_t ah = smem_u32(a_hi + b * Geo::A_BYTES), al = smem_u32(a_lo + b * Geo::A_BYTES);
+                // D = Al Bh^T + Ah Bl^T + Ah Bh^T (small terms first), K = 16 per instruction
 #pragma unroll
-            for (int ks = 0; ks < K / 16; ++ks)
-                tc_mma_f16(tmem, tc_smem_desc(ah + ks * 256, Geo::LBO, Geo::SBO), tc_smem_desc(bl + ks * 256, Geo::LBO, Geo::SBO),
-                           idesc, 1);
+                for (int ks = 0; ks < K / 16; ++ks)
+                    tc_mma_f16(d, tc_smem_desc(al + ks * 256, Geo::LBO, Geo::SBO),
+                               tc_smem_desc(bh + ks * 256, Geo::LBO, Geo::SBO), idesc, ks);
 #pragma unroll
-            for (int ks = 0; ks < K / 16; ++ks)
-                tc_mma_f16(tmem, tc_smem_desc(ah + ks * 256, Geo::LBO, Geo::SBO), tc_smem_desc(bh + ks * 256, Geo::LBO, Geo::SBO),
-                           idesc, 1);
+                for (int ks = 0; ks < K / 16; ++ks)
+                    tc_mma_f16(d, tc_smem_desc(ah + ks * 256, Geo::LBO, Geo::SBO),
+                               tc_smem_desc(bl + ks * 256, Geo::LBO, Geo::SBO), idesc, 1);
+#pragma unroll
+                for (int ks = 0; ks < K / 16; ++ks)
+                    tc_mma_f16(d, tc_smem_desc(ah + ks * 256, Geo::LBO, Geo::SBO),
+                               tc_smem_desc(bh + ks * 256, Geo::LBO, Geo::SBO), idesc, 1);
+            }
             tc_commit(bar);
         }
         ok = __syncthreads_and(mbar_wait(bar, phase, kDirectWaitNs) ? 1 : 0);
         phase ^= 1u;
         if (!ok) break;
         tc_fence_after();
-        // Row tid of D: warp w owns TMEM lanes 32w..32w+31.
-        const int row = tid;
+        // Row tid of the tile: warp w reads TMEM lanes 32 (w % 4) .. + 31 of block w / 4.
+        const int row = tid, warp = tid >> 5;
         const float inv_sc = PREC == 0 ? __uint_as_float((uint32_t)(127 - 14 + s_exp[row]) << 23) : 1.f;
-        const uint32_t taddr = tmem + ((uint32_t)((tid >> 5) * 32) << 16);
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * K);
         float4* srow = reinterpret_cast<float4*>(stage + row * Geo::PITCH);
 #pragma unroll
         for (int c0 = 0; c0 < N; c0 += 8) {
@@ -195,7 +204,7 @@ __global__ void __launch_bounds__(kDirectRows) k_dft_direct_umma(const float2* i
         constexpr int PPR = N / 2;  // 16-byte pieces per row
 #pragma unroll
         for (int i = 0; i < PPR; ++i) {
-            const int p = tid + i * kDirectRows;
+            const int p = tid + i * ROWS;
             const int r = p / PPR;
             if (r < nvalid) dst[p] = *reinterpret_cast<const float4*>(stage + r * Geo::PITCH + (p % PPR) * 16);
         }
@@ -245,8 +254,8 @@ template <int N>
 DirectVariant make_direct_variant() {
     DirectVariant v{};
     v.n = N;
-    v.rows = kDirectRows;
-    v.tpb = kDirectRows;
+    v.rows = DirectGeom<N>::ROWS;
+    v.tpb = DirectGeom<N>::ROWS;
     v.smem = DirectGeom<N>::SMEM;
     v.bmat_bytes = DirectGeom<N>::B_BYTES;
     v.tmem_cols = (int)DirectGeom<N>::COLS;
