@@ -40,7 +40,9 @@ constexpr uint32_t tmem_cols_for(int k) { return k <= 32 ? 32u : (k <= 64 ? 64u 
 
 template <int N>
 struct DirectGeom {
-    static constexpr int BLK = N <= 16 ? 4 : (N <= 32 ? 2 : 1);  // 128-row blocks per tile (M = 128 MMAs)
+    // 128-row blocks per tile (M = 128 MMAs): the choice that maximises resident warps per SM under the
+    // shared-memory (A operands or output staging, plus B) and tensor-memory budgets
+    static constexpr int BLK = N == 8 ? 4 : ((N == 16 || N == 40 || N == 64) ? 2 : 1);
     static constexpr int ROWS = kDirectRows * BLK;               // transforms per tile = threads per CTA
     static constexpr int K = 2 * N;                              // [re parts | im parts]
     static constexpr int LBO = 128;                              // K-adjacent core matrices
@@ -64,7 +66,8 @@ __global__ void __launch_bounds__(DirectGeom<N>::ROWS) k_dft_direct_umma(const f
                                                                          long long batch, int* status) {
     using Geo = DirectGeom<N>;
     constexpr int K = Geo::K, BLK = Geo::BLK, ROWS = Geo::ROWS, CPR = N / 8;  // 8-complex chunks per row
-    constexpr int G = CPR <= 1 ? 1 : (CPR <= 2 ? 2 : (CPR <= 4 ? 4 : 8));
+    constexpr int G = CPR <= 1 ? 1 : (CPR <= 2 ? 2 : (CPR <= 4 ? 4 : 8));  // chunk slots per row (power of 2)
+    constexpr int LPR = G < 4 ? G : 4, H = G / LPR;                          // lanes per row, chunks per lane
     extern __shared__ __align__(1024) uint8_t dsm[];
     uint8_t* const a_hi = dsm;                         // BLK blocks of 128 x K halves
     uint8_t* const a_lo = dsm + BLK * Geo::A_BYTES;
@@ -98,58 +101,68 @@ __global__ void __launch_bounds__(DirectGeom<N>::ROWS) k_dft_direct_umma(const f
         const long long r0 = tile * ROWS;
         const int nvalid = (int)min((long long)ROWS, batch - r0);
         const float4* src = reinterpret_cast<const float4*>(in + r0 * N);
-        // Load, scale and split.  Each row is served by G lanes (G = CPR rounded up
-        // to a power of two, so that a row's lanes form an aligned group for the
-        // shuffle reduction); lane j < CPR of the group holds complex 8j..8j+7.
+        // Load, scale and split.  A row's G chunks (8 complex each) are held by LPR
+        // lanes of one warp (H chunks per lane); a quarter-warp (8 lanes) covers 8
+        // consecutive rows with the same chunk index, so its 16-byte stores into the
+        // core-matrix layout (16 bytes per row per core matrix) hit 8 distinct bank
+        // groups, and the row's lanes are 8 apart for the shuffle reduction.
+        {
+            const int lane = tid & 31, warp = tid >> 5;
+            const int b8 = lane & 7, q = lane >> 3;
 #pragma unroll
-        for (int it = 0; it < G; ++it) {
-            const int row = it * (ROWS / G) + tid / G, j = tid % G;
-            const bool have = j < CPR;
-            float re[8], im[8];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (have && row < nvalid) v = src[(row * N + 8 * j) / 2 + h];
-                re[2 * h] = v.x;
-                im[2 * h] = v.y;
-                re[2 * h + 1] = v.z;
-                im[2 * h + 1] = v.w;
-            }
-            if constexpr (PREC == 0) {
-                // exact power-of-two scale per row to [2^14, 2^15) (FP16 range)
+            for (int it = 0; it < LPR; ++it) {
+                const int row = it * (ROWS / LPR) + warp * (32 / LPR) + b8 + 8 * (q / LPR);
+                float re[H][8], im[H][8];
                 float m = 0.f;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) m = fmaxf(m, fmaxf(fabsf(re[e]), fabsf(im[e])));
+                for (int hh = 0; hh < H; ++hh) {
+                    const int j = q % LPR + LPR * hh;
 #pragma unroll
-                for (int off = G / 2; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
-                int ex = (int)((__float_as_uint(m) >> 23) & 0xff) - 127;
-                if (!(m > 0.f)) ex = 0;
-                ex = max(-100, min(100, ex));
-                if (j == 0) s_exp[row] = ex;
-                const float sc = __uint_as_float((uint32_t)(127 + 14 - ex) << 23);
+                    for (int h = 0; h < 4; ++h) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (j < CPR && row < nvalid) v = src[(row * N + 8 * j) / 2 + h];
+                        re[hh][2 * h] = v.x;
+                        im[hh][2 * h] = v.y;
+                        re[hh][2 * h + 1] = v.z;
+                        im[hh][2 * h + 1] = v.w;
+                    }
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    re[e] *= sc;
-                    im[e] *= sc;
+                    for (int e = 0; e < 8; ++e) m = fmaxf(m, fmaxf(fabsf(re[hh][e]), fabsf(im[hh][e])));
                 }
-            }
-            if (have) {
-                uint32_t hr[4], lr[4], hi_[4], li[4];
+                float sc = 1.f;
+                if constexpr (PREC == 0) {
+                    // exact power-of-two scale per row to [2^14, 2^15) (FP16 range)
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    float a, b;
-                    hr[p] = pack_hi<PREC>(re[2 * p], re[2 * p + 1], a, b);
-                    lr[p] = pack_lo<PREC>(a, b);
-                    hi_[p] = pack_hi<PREC>(im[2 * p], im[2 * p + 1], a, b);
-                    li[p] = pack_lo<PREC>(a, b);
+                    for (int off = 8; off < 8 * LPR; off <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+                    int ex = (int)((__float_as_uint(m) >> 23) & 0xff) - 127;
+                    if (!(m > 0.f)) ex = 0;
+                    ex = max(-100, min(100, ex));
+                    if (q % LPR == 0) s_exp[row] = ex;
+                    sc = __uint_as_float((uint32_t)(127 + 14 - ex) << 23);
                 }
                 const uint32_t blk = (uint32_t)(row / kDirectRows) * Geo::A_BYTES;
                 const int rr = row % kDirectRows;
-                const uint32_t o_re = blk + k_offset(rr, j, Geo::SBO), o_im = blk + k_offset(rr, N / 8 + j, Geo::SBO);
-                *reinterpret_cast<uint4*>(a_hi + o_re) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
-                *reinterpret_cast<uint4*>(a_lo + o_re) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
-                *reinterpret_cast<uint4*>(a_hi + o_im) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
-                *reinterpret_cast<uint4*>(a_lo + o_im) = make_uint4(li[0], li[1], li[2], li[3]);
+#pragma unroll
+                for (int hh = 0; hh < H; ++hh) {
+                    const int j = q % LPR + LPR * hh;
+                    if (j < CPR) {
+                        uint32_t hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            float a, b;
+                            hr[p] = pack_hi<PREC>(re[hh][2 * p] * sc, re[hh][2 * p + 1] * sc, a, b);
+                            lr[p] = pack_lo<PREC>(a, b);
+                            hi_[p] = pack_hi<PREC>(im[hh][2 * p] * sc, im[hh][2 * p + 1] * sc, a, b);
+                            li[p] = pack_lo<PREC>(a, b);
+                        }
+                        const uint32_t o_re = blk + k_offset(rr, j, Geo::SBO);
+                        const uint32_t o_im = blk + k_offset(rr, N / 8 + j, Geo::SBO);
+                        *reinterpret_cast<uint4*>(a_hi + o_re) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+                        *reinterpret_cast<uint4*>(a_lo + o_re) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+                        *reinterpret_cast<uint4*>(a_hi + o_im) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+                        *reinterpret_cast<uint4*>(a_lo + o_im) = make_uint4(li[0], li[1], li[2], li[3]);
+                    }
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
