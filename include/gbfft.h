@@ -229,6 +229,42 @@ gbfft_status gbfft_wisdom_import(const char *path, int require_same_gpu);
 gbfft_status gbfft_wisdom_forget(void);
 
 /*
+ * Factorisation-formula front end (the operator vocabulary of Table I, the
+ * paper's own input language, Sec. IV-A): DFT(n), I(n), A ⊗ B (or `A kron B`),
+ * A · B (or `A * B`, `A . B`), twiddle(N, M) = D^N_M, Permute(N, K) =
+ * Pi^N_K, parentheses; ⊗ and · are right-associative at one precedence level
+ * (the paper's grammar); UTF-8 text.  A program line such as Listing 1's
+ * `var result = (DFT(2) ⊗ I(2)) · twiddle(4,2) · (I(2) ⊗ DFT(2)) · Permute(4,2)
+ * · InputComplex;` is accepted: the `var name =` prefix, a trailing input
+ * identifier and `;` are ignored.
+ *
+ * gbfft_formula_check: parses `formula` and checks symbolically that it
+ * denotes DFT_N through Eq. 2, (DFT_K ⊗ I_M) · twiddle(N, M) · (I_K ⊗ DFT_M) ·
+ * Permute(N, K) with N = K*M, recursively (each DFT factor may be such a
+ * product; Eq. 1 is N = 4).  On success writes N, the outermost K (0 when the
+ * formula is a single DFT(N)), and the DFT leaf sizes in the order the product
+ * applies them (rightmost first; at most `max_leaves` written, *nleaves = the
+ * full count).  Host only: no CUDA call.  Errors: INVALID_ARG (syntax,
+ * dimension mismatch, or not a DFT factorisation), with a message in `err`
+ * (`err_len` bytes, may be NULL/0).
+ */
+gbfft_status gbfft_formula_check(const char *formula, int64_t *n, int *leaves, int max_leaves, int *nleaves,
+                                 int64_t *k_outer, char *err, size_t err_len);
+
+/*
+ * A plan for the transform a checked formula denotes, following the formula
+ * as literally as the compiled kernels allow.  *match (may be NULL): 2 = the
+ * formula's own factorisation (a single-pass plan whose Stockham radix
+ * sequence is the formula's leaf sequence, or Eq. 2's two-pass plan with the
+ * formula's outermost split K x M over plain DFT(K), DFT(M) factors); 1 = the
+ * same radices in another stage order, or the outermost split with the inner
+ * factors on the column kernels' own schedules; 0 = the default plan for N.
+ * Errors as gbfft_formula_check (INVALID_ARG) and gbfft_plan_create.
+ */
+gbfft_status gbfft_plan_create_formula(gbfft_plan *out, const char *formula, int64_t batch, int direction, int dtype,
+                                       int *match);
+
+/*
  * Ragged batches: `count` independent transforms of uneven lengths n[i]
  * (any 1 <= n[i] <= 8192 whose prime factors are 2, 3, 5 and 7; others give
  * UNSUPPORTED_SIZE), transform i occupying complex elements

@@ -1,10 +1,12 @@
 // The C ABI of include/gbfft.h: plans, execution, variant registry, status.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "internal.h"
 
@@ -470,6 +472,58 @@ gbfft_status gbfft_plan_create_twopass(gbfft_plan* out, int64_t n, int64_t batch
         k_outer = kk;
     }
     return create(out, n, batch, direction, dtype, -1, k_outer);
+}
+
+// A plan that follows a factorisation formula as literally as the compiled
+// kernels allow; *match: 2 = the formula's own schedule (single pass with its
+// radix sequence, or Eq. 2's two passes with its outermost split over plain
+// DFT factors), 1 = the same radices in another stage order or the outermost
+// split with the inner factors on the column kernels' own schedules, 0 = the
+// default plan for N (the formula still denotes DFT_N).
+gbfft_status gbfft_plan_create_formula(gbfft_plan* out, const char* formula, int64_t batch, int direction, int dtype,
+                                       int* match) {
+    if (out) *out = nullptr;
+    if (match) *match = 0;
+    if (!out) return GBFFT_ERR_INVALID_ARG;
+    int64_t n = 0, k_top = 0;
+    std::vector<int64_t> leaves;
+    bool bare = false;
+    if (!formula_plan_choice(formula, &n, &leaves, &k_top, &bare)) return GBFFT_ERR_INVALID_ARG;
+    int exact = -1, multi = -1;
+    if (dtype == GBFFT_C2C_F32 || dtype == GBFFT_C2C_F64) {
+        const RowsVariant* cands[kMaxVariantsPerSize];
+        const int nc = dtype == GBFFT_C2C_F32 ? rows_variants_for(n, cands, kMaxVariantsPerSize)
+                                              : rows_variants_f64_for(n, cands, kMaxVariantsPerSize);
+        std::vector<int64_t> want = leaves;
+        std::sort(want.begin(), want.end());
+        for (int v = 0; v < nc && v < kMaxVariantsPerSize; ++v) {
+            std::vector<int64_t> have(cands[v]->radix, cands[v]->radix + cands[v]->nstages);
+            if (exact < 0 && have == leaves) exact = v;
+            std::sort(have.begin(), have.end());
+            if (multi < 0 && have == want) multi = v;
+        }
+    }
+    int64_t kk = 0, mm = 0;
+    const bool split_ok = dtype == GBFFT_C2C_F32 && k_top > 0 && choose_split(n, k_top, &kk, &mm);
+    gbfft_status st;
+    int m = 0;
+    if (exact >= 0) {
+        st = create(out, n, batch, direction, dtype, exact, 0);
+        m = 2;
+    } else if (split_ok && bare) {
+        st = create(out, n, batch, direction, dtype, -1, k_top);
+        m = 2;
+    } else if (multi >= 0) {
+        st = create(out, n, batch, direction, dtype, multi, 0);
+        m = 1;
+    } else if (split_ok) {
+        st = create(out, n, batch, direction, dtype, -1, k_top);
+        m = 1;
+    } else {
+        st = create(out, n, batch, direction, dtype, -1, 0);
+    }
+    if (st == GBFFT_OK && match) *match = m;
+    return st;
 }
 
 gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_stream) {

@@ -1,0 +1,337 @@
+// Factorisation-formula front end: the operator vocabulary of Table I
+// (DFT(n), I(n), A ⊗ B, A · B, twiddle(N, M), Permute(N, K)), parsed on the
+// host and checked to denote DFT_N by the Cooley-Tukey identity of Eq. 2,
+//     DFT_N = (DFT_K ⊗ I_M) · twiddle(N, M) · (I_K ⊗ DFT_M) · Permute(N, K),  N = K M,
+// applied recursively (either DFT factor may itself be such a product; Eq. 1
+// is the case N = 4).  twiddle(N, M) is the diagonal D^N_M and Permute(N, K)
+// the stride permutation Pi^N_K of Eq. 2 (their argument order follows the
+// subscripts of Eq. 2).  A checked formula then selects the execution plan:
+// its DFT leaves, in the order the product applies them (rightmost first),
+// are the radix schedule of a single-pass plan, and its outermost split K x M
+// is the k_outer of a two-pass plan.
+//
+// Syntax (after the paper's grammar, Sec. IV-A): factors joined by ⊗ (or the
+// ASCII word `kron`) and · (or `*` or `.`), both right-associative at one
+// precedence level, parentheses, integer arguments.  A formula may be written
+// as a program line, `var result = <formula> · InputComplex;`: a trailing
+// identifier (the input vector) and the `var name =` prefix and `;` are
+// accepted and ignored.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace gbfft {
+namespace {
+
+enum NodeKind { kDft, kIdent, kTwiddle, kPermute, kKron, kProd, kInput };
+
+struct Node {
+    NodeKind kind;
+    int64_t a = 0, b = 0;           // integer arguments
+    std::unique_ptr<Node> l, r;     // operands of kKron / kProd
+};
+
+struct Parser {
+    const char* s;
+    size_t pos = 0;
+    std::string err;
+
+    explicit Parser(const char* text) : s(text) {}
+
+    void skip() {
+        while (s[pos] == ' ' || s[pos] == '\t' || s[pos] == '\n' || s[pos] == '\r') ++pos;
+    }
+    bool fail(const std::string& m) {
+        if (err.empty()) err = m + " at offset " + std::to_string(pos);
+        return false;
+    }
+    bool accept(const char* tok) {
+        skip();
+        const size_t n = std::strlen(tok);
+        if (std::strncmp(s + pos, tok, n) == 0) {
+            pos += n;
+            return true;
+        }
+        return false;
+    }
+    static bool ident_char(char c) {
+        return (c >= 'a' && c <= 'z') || (c >= 'A' && c <= 'Z') || (c >= '0' && c <= '9') || c == '_';
+    }
+    bool word(std::string* out) {
+        skip();
+        const size_t b = pos;
+        if (!((s[pos] >= 'a' && s[pos] <= 'z') || (s[pos] >= 'A' && s[pos] <= 'Z') || s[pos] == '_')) return false;
+        while (ident_char(s[pos])) ++pos;
+        *out = std::string(s + b, pos - b);
+        return true;
+    }
+    bool integer(int64_t* v) {
+        skip();
+        if (s[pos] < '0' || s[pos] > '9') return fail("expected an integer");
+        int64_t x = 0;
+        while (s[pos] >= '0' && s[pos] <= '9') {
+            x = x * 10 + (s[pos] - '0');
+            if (x > ((int64_t)1 << 40)) return fail("integer too large");
+            ++pos;
+        }
+        *v = x;
+        return true;
+    }
+    // Binary operator: 1 = Kronecker, 2 = product, 0 = none.
+    int op() {
+        skip();
+        const size_t save = pos;
+        if (accept("\xE2\x8A\x97")) return 1;  // ⊗
+        if (accept("\xC2\xB7")) return 2;      // ·
+        if (accept("*") || accept(".")) return 2;
+        std::string w;
+        if (word(&w) && w == "kron") return 1;
+        pos = save;
+        return 0;
+    }
+    bool args(int count, int64_t* a, int64_t* b) {
+        if (!accept("(")) return fail("expected '('");
+        if (!integer(a)) return false;
+        if (count == 2) {
+            if (!accept(",")) return fail("expected ','");
+            if (!integer(b)) return false;
+        }
+        if (!accept(")")) return fail("expected ')'");
+        return true;
+    }
+    std::unique_ptr<Node> primary() {
+        skip();
+        if (accept("(")) {
+            auto e = expr();
+            if (!e) return nullptr;
+            if (!accept(")")) {
+                fail("expected ')'");
+                return nullptr;
+            }
+            return e;
+        }
+        std::string w;
+        if (!word(&w)) {
+            fail("expected a factor");
+            return nullptr;
+        }
+        auto n = std::make_unique<Node>();
+        bool ok = true;
+        if (w == "DFT" || w == "dft") {
+            n->kind = kDft;
+            ok = args(1, &n->a, nullptr);
+        } else if (w == "I" || w == "identity") {
+            n->kind = kIdent;
+            ok = args(1, &n->a, nullptr);
+        } else if (w == "twiddle") {
+            n->kind = kTwiddle;
+            ok = args(2, &n->a, &n->b);
+        } else if (w == "Permute" || w == "permute") {
+            n->kind = kPermute;
+            ok = args(2, &n->a, &n->b);
+        } else {
+            n->kind = kInput;  // an input vector such as InputComplex
+        }
+        return ok ? std::move(n) : nullptr;
+    }
+    // expr := primary ((⊗ | ·) expr)?   (right-associative, one precedence level)
+    std::unique_ptr<Node> expr() {
+        auto l = primary();
+        if (!l) return nullptr;
+        const int o = op();
+        if (o == 0) return l;
+        auto r = expr();
+        if (!r) return nullptr;
+        auto n = std::make_unique<Node>();
+        n->kind = o == 1 ? kKron : kProd;
+        n->l = std::move(l);
+        n->r = std::move(r);
+        return n;
+    }
+    std::unique_ptr<Node> program() {
+        skip();
+        const size_t save = pos;
+        std::string w;
+        if (word(&w) && w == "var") {  // var <name> = <formula> ;
+            std::string name;
+            if (!word(&name) || !accept("=")) {
+                fail("expected 'var <name> ='");
+                return nullptr;
+            }
+        } else {
+            pos = save;
+        }
+        auto e = expr();
+        if (!e) return nullptr;
+        accept(";");
+        skip();
+        if (s[pos] != '\0') {
+            fail("unexpected text after the formula");
+            return nullptr;
+        }
+        return e;
+    }
+};
+
+// Matrix dimension of a node (0 if ill-formed, with a message).
+int64_t dim(const Node* n, std::string* err) {
+    switch (n->kind) {
+        case kDft:
+        case kIdent:
+            if (n->a < 1) return *err = "DFT(n) and I(n) need n >= 1", 0;
+            return n->a;
+        case kTwiddle:
+        case kPermute:
+            if (n->a < 1 || n->b < 1 || n->a % n->b != 0)
+                return *err = "twiddle(N, M) and Permute(N, K) need a divisor of N", 0;
+            return n->a;
+        case kInput:
+            return *err = "an input vector may only be the last factor of the formula", 0;
+        case kKron: {
+            const int64_t a = dim(n->l.get(), err), b = dim(n->r.get(), err);
+            if (!a || !b) return 0;
+            if (a > ((int64_t)1 << 40) / b) return *err = "dimension too large", 0;
+            return a * b;
+        }
+        case kProd: {
+            const int64_t a = dim(n->l.get(), err), b = dim(n->r.get(), err);
+            if (!a || !b) return 0;
+            if (a != b) return *err = "factors of a product must have equal dimensions", 0;
+            return a;
+        }
+    }
+    return 0;
+}
+
+void flatten_product(const Node* n, std::vector<const Node*>* out) {
+    if (n->kind == kProd) {
+        flatten_product(n->l.get(), out);
+        flatten_product(n->r.get(), out);
+    } else {
+        out->push_back(n);
+    }
+}
+
+struct DftForm {
+    int64_t n = 0;
+    int64_t k_top = 0;            // outermost split N = K * M (0: a single DFT(n) leaf)
+    bool bare = false;            // the outermost split's DFT factors are DFT(K), DFT(M) leaves
+    std::vector<int64_t> leaves;  // DFT leaf sizes in application order
+};
+
+// Whether n denotes DFT_N: a DFT(n) leaf, or Eq. 2's four factors with DFT
+// factors that themselves denote DFTs.
+bool as_dft(const Node* n, DftForm* f, std::string* err) {
+    if (n->kind == kDft) {
+        f->n = n->a;
+        f->k_top = 0;
+        f->leaves = {n->a};
+        return true;
+    }
+    if (n->kind != kProd) return *err = "not a DFT: expected DFT(n) or a product of Eq. 2's four factors", false;
+    std::vector<const Node*> fs;
+    flatten_product(n, &fs);
+    if (fs.size() == 1) return as_dft(fs[0], f, err);
+    if (fs.size() != 4)
+        return *err = "not a DFT: Eq. 2 has four factors (DFT_K (x) I_M) . twiddle(N,M) . (I_K (x) DFT_M) . Permute(N,K)",
+               false;
+    const Node *f1 = fs[0], *f2 = fs[1], *f3 = fs[2], *f4 = fs[3];
+    if (f1->kind != kKron || f1->r->kind != kIdent)
+        return *err = "first factor must be (DFT_K (x) I_M)", false;
+    if (f3->kind != kKron || f3->l->kind != kIdent) return *err = "third factor must be (I_K (x) DFT_M)", false;
+    if (f2->kind != kTwiddle) return *err = "second factor must be twiddle(N, M)", false;
+    if (f4->kind != kPermute) return *err = "fourth factor must be Permute(N, K)", false;
+    DftForm x, y;
+    if (!as_dft(f1->l.get(), &x, err) || !as_dft(f3->r.get(), &y, err)) return false;
+    const int64_t K = x.n, M = y.n, N = K * M;
+    if (f1->r->a != M) return *err = "first factor: I_M must match DFT_M of the third factor", false;
+    if (f3->l->a != K) return *err = "third factor: I_K must match DFT_K of the first factor", false;
+    if (f2->a != N || f2->b != M) return *err = "second factor must be twiddle(N, M) with N = K*M", false;
+    if (f4->a != N || f4->b != K) return *err = "fourth factor must be Permute(N, K) with N = K*M", false;
+    f->n = N;
+    f->k_top = K;
+    f->bare = x.k_top == 0 && y.k_top == 0;
+    f->leaves = y.leaves;  // DFT_M runs first (after the permutation), then DFT_K
+    f->leaves.insert(f->leaves.end(), x.leaves.begin(), x.leaves.end());
+    return true;
+}
+
+gbfft_status check(const char* text, DftForm* f, std::string* err) {
+    if (!text) return *err = "null formula", GBFFT_ERR_INVALID_ARG;
+    Parser p(text);
+    auto root = p.program();
+    if (!root) return *err = p.err, GBFFT_ERR_INVALID_ARG;
+    // Strip a trailing input vector: <formula> · InputComplex.
+    const Node* body = root.get();
+    if (body->kind == kInput) return *err = "the formula has no operator", GBFFT_ERR_INVALID_ARG;
+    std::unique_ptr<Node> owned;
+    if (body->kind == kProd) {
+        // find the rightmost factor of the top-level product chain
+        Node* parent = nullptr;
+        Node* cur = root.get();
+        while (cur->kind == kProd && cur->r->kind == kProd) {
+            parent = cur;
+            cur = cur->r.get();
+        }
+        if (cur->kind == kProd && cur->r->kind == kInput) {
+            if (parent) {
+                parent->r = std::move(cur->l);
+            } else {
+                owned = std::move(root->l);
+                body = owned.get();
+            }
+        }
+    }
+    if (!dim(body, err)) return GBFFT_ERR_INVALID_ARG;
+    if (!as_dft(body, f, err)) return GBFFT_ERR_INVALID_ARG;
+    return GBFFT_OK;
+}
+
+void put_err(const std::string& e, char* buf, size_t len) {
+    if (!buf || len == 0) return;
+    std::snprintf(buf, len, "%s", e.c_str());
+}
+
+}  // namespace
+
+bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* leaves, int64_t* k_top, bool* bare) {
+    DftForm f;
+    std::string err;
+    if (check(text, &f, &err) != GBFFT_OK) return false;
+    *n = f.n;
+    *leaves = f.leaves;
+    *k_top = f.k_top;
+    *bare = f.bare;
+    return true;
+}
+
+}  // namespace gbfft
+
+using namespace gbfft;
+
+extern "C" {
+
+gbfft_status gbfft_formula_check(const char* formula, int64_t* n, int* leaves, int max_leaves, int* nleaves,
+                                 int64_t* k_outer, char* err, size_t err_len) {
+    DftForm f;
+    std::string e;
+    const gbfft_status st = check(formula, &f, &e);
+    if (st != GBFFT_OK) {
+        put_err(e, err, err_len);
+        return st;
+    }
+    put_err("", err, err_len);
+    if (n) *n = f.n;
+    if (k_outer) *k_outer = f.k_top;
+    if (nleaves) *nleaves = (int)f.leaves.size();
+    if (leaves)
+        for (int i = 0; i < (int)f.leaves.size() && i < max_leaves; ++i) leaves[i] = (int)f.leaves[i];
+    return GBFFT_OK;
+}
+
+}  // extern "C"

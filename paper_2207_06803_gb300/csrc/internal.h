@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "gbfft.h"
 
@@ -122,6 +123,11 @@ int ragged_queue_order(const RaggedState* r);
 // Radix schedule the plan uses for length n (stage count; 0 if n is absent).
 int ragged_schedule(const RaggedState* r, int64_t n, int* radix);
 bool ragged_supported(int64_t n);
+
+// Factorisation-formula front end (formula.cu): whether `text` denotes DFT_n by
+// Eq. 2; its DFT leaves in application order, outermost split K (0 if none) and
+// whether that split's DFT factors are plain DFT(K), DFT(M) leaves.
+bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* leaves, int64_t* k_top, bool* bare);
 
 // Planner wisdom (autotune.cu): the autotuned choice for (n, dtype, direction).
 void wisdom_load_env_once();

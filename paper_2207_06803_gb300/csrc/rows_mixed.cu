@@ -9,6 +9,8 @@
 namespace gbfft {
 
 static const RowsVariant kMixed[] = {
+    // N = 4 as two radix-2 stages (Eq. 1's factorisation; an alternative to the radix-4 codelet)
+    GBFFT_ROWS(4, 4, 128, 0, 2, 2),
     GBFFT_ROWS(3, 3, 128, 0, 3),
     GBFFT_ROWS(6, 6, 128, 4, 3, 2),
     GBFFT_ROWS_T(6, 768, 256, 0, 3, 2),

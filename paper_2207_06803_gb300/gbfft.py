@@ -80,6 +80,9 @@ PROTOTYPES = {
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
     "gbfft_ragged_queue_order": (_c_int, [_c_vp]),
     "gbfft_ragged_schedule": (_c_int, [_c_vp, _c_i64, _c_intp]),
+    "gbfft_formula_check": (_c_int, [ctypes.c_char_p, _c_i64p, _c_intp, _c_int, _c_intp, _c_i64p, ctypes.c_char_p,
+                                     ctypes.c_size_t]),
+    "gbfft_plan_create_formula": (_c_int, [ctypes.POINTER(_c_vp), ctypes.c_char_p, _c_i64, _c_int, _c_int, _c_intp]),
     "gbfft_ragged_set_item_ready": (_c_int, [_c_vp, _c_i64, _c_int]),
     "gbfft_ragged_set_wait_limit": (_c_int, [_c_vp, _c_i64]),
     "gbfft_server_create": (_c_int, [ctypes.POINTER(_c_vp), _c_size, _c_int, _c_int]),
@@ -302,6 +305,29 @@ def gbfft_ragged_num_items(plan: int) -> int:
 
 def gbfft_ragged_tile_split(plan: int, n: int) -> int:
     return int(lib().gbfft_ragged_tile_split(plan, n))
+
+
+def gbfft_formula_check(formula: str) -> dict:
+    """Check a Table I factorisation formula; {'n', 'k_outer', 'leaves'} or GbfftError (message in .args)."""
+    n, k = ctypes.c_int64(), ctypes.c_int64()
+    leaves = (ctypes.c_int * 64)()
+    nl = ctypes.c_int()
+    err = ctypes.create_string_buffer(256)
+    rc = lib().gbfft_formula_check(formula.encode("utf-8"), ctypes.byref(n), leaves, 64, ctypes.byref(nl),
+                                   ctypes.byref(k), err, 256)
+    if rc != 0:
+        raise GbfftError(rc, "gbfft_formula_check: " + err.value.decode("utf-8", "replace"))
+    return {"n": n.value, "k_outer": k.value, "leaves": list(leaves[: min(nl.value, 64)])}
+
+
+def gbfft_plan_create_formula(formula: str, batch: int, direction: int = GBFFT_FORWARD,
+                              dtype: int = GBFFT_C2C_F32) -> tuple[int, int]:
+    """(plan handle, match level) for a factorisation formula."""
+    h = ctypes.c_void_p()
+    m = ctypes.c_int()
+    _check(lib().gbfft_plan_create_formula(ctypes.byref(h), formula.encode("utf-8"), batch, direction, dtype,
+                                           ctypes.byref(m)), "gbfft_plan_create_formula")
+    return h.value, m.value
 
 
 def gbfft_ragged_schedule(plan: int, n: int) -> list[int]:
