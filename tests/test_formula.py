@@ -234,7 +234,7 @@ def test_eq1_formula_plan_reproduces_the_worked_example():
 @pytest.mark.parametrize("radices,want_match,want_k", [
     ([16, 16, 16], 2, 0),      # a compiled single-pass schedule, same stage order
     ([16, 4, 16], 1, 0),       # the same radices in another order
-    ([64, 128], 2, 64),        # N = 8192: Eq. 2's two passes with the formula's split
+    ([64, 128], 2, 128),       # N = 8192: Eq. 2 as two passes with the formula's split K = 128
     ([2] * 10, 0, 0),          # no compiled radix-2 schedule: the default plan, still DFT_1024
 ])
 def test_formula_plans_match_the_oracle(radices, want_match, want_k):
