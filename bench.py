@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
-    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving", "f64"], default="sweep",
+    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving", "f64", "nd"], default="sweep",
                     help="sweep (default, the headline line) or one of the other configurations")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -433,7 +433,7 @@ def other_configs(args):
     small = argparse.Namespace(**vars(args))
     small.steps = 40
     for name, fn in (("twopass", run_twopass), ("tc", lambda a: run_tc(a, dists=("uniform",))),
-                     ("ragged", run_ragged), ("f64", run_f64),
+                     ("ragged", run_ragged), ("f64", run_f64), ("nd", run_nd),
                      ("serving", lambda a: run_serving(a, rates=(1000, 10000), scale=0.2, serial_rates=(1000,)))):
         try:
             r = fn(small)
@@ -445,6 +445,9 @@ def other_configs(args):
         elif name == "tc":
             out[name] = {k: {"gbs": round(v["gbs"], 1), "vs_fp32": round(v["vs_fp32"], 3),
                              "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for k, v in r["results"].items()}
+        elif name == "nd":
+            out[name] = {k: {"alg_gbs": round(v["alg_gbs"], 1), "frac_actual_of_hbm": round(v["frac_actual_of_hbm"], 3)}
+                         for k, v in r["per_shape"].items()}
         elif name == "f64":
             out[name] = {n: {"fwd_gflops": round(v["fwd"]["gflops"], 1), "fwd_gbs": round(v["fwd"]["gbs"], 1),
                              "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for n, v in r["per_size"].items()}
@@ -533,6 +536,34 @@ def run_twopass(args):
                         "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak}
     return {"config": "twopass", "metric": "two-pass Eq. 2 c2c GB/s (16 B/point algorithmic)",
             "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_size": rows}
+
+
+def run_nd(args):
+    """Multi-dimensional transforms (last axis by the row kernel, the others by the column kernel, in
+    place): 2-D and 3-D shapes at 2^26 points per call; GB/s on 16 B/point (algorithmic) and on the
+    HBM traffic of one read and one write per axis pass."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peak, src = _peak()
+    flat = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL)
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    d_out = torch.empty_like(d_in)
+    rows = {}
+    for dims in ((64, 4096), (512, 1024), (128, 512), (64, 64, 256), (32, 128, 1024), (512, 8, 1024)):
+        total = 1
+        for v in dims:
+            total *= v
+        batch = TOTAL // total
+        with gbfft.Plan(dims, batch, -1) as p:
+            ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+        alg = 16.0 * total * batch / (ms * 1e-3) / 1e9
+        rows["x".join(map(str, dims))] = {"batch": batch, "ms": ms, "alg_gbs": alg,
+                                          "actual_gbs": alg * len(dims), "frac_actual_of_hbm": alg * len(dims) / peak}
+    return {"config": "nd", "metric": "multi-dimensional c2c GB/s (16 B/point algorithmic; one HBM round trip per axis)",
+            "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_shape": rows}
 
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured figure exists for it)
@@ -777,7 +808,7 @@ def main():
         return run_reference(args)
     if args.config != "sweep":
         fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving,
-              "f64": run_f64}[args.config]
+              "f64": run_f64, "nd": run_nd}[args.config]
         print(json.dumps(fn(args)), flush=True)
         return 0
     return run_gpu(args)

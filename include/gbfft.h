@@ -229,6 +229,27 @@ gbfft_status gbfft_wisdom_import(const char *path, int require_same_gpu);
 gbfft_status gbfft_wisdom_forget(void);
 
 /*
+ * Multi-dimensional transforms: `batch` row-major complex64 arrays of shape
+ * dims[0] x ... x dims[rank-1] (rank 1..3, the last axis contiguous, array i
+ * at element i * prod(dims)), each transformed by DFT_{dims[0]} ⊗ ... ⊗
+ * DFT_{dims[rank-1]} (the Kronecker product of Table I applied to whole
+ * transforms; direction and scaling as gbfft_plan_create).  Execution: the
+ * last axis by the single-pass row kernel, then every other axis, last to
+ * first, by the column kernel of Eq. 2's second pass, in place in `out`.
+ * Sizes: dims[rank-1] a single-pass length and a multiple of 16; the other
+ * axes column lengths (8, 16, 32, 48, 64, 80, 96, 112, 128, 256, 512); else
+ * UNSUPPORTED_SIZE.  FP32 only (INVALID_ARG otherwise).  Executed with
+ * gbfft_execute / gbfft_execute_host; gbfft_plan_info reports n = prod(dims)
+ * and the last axis' radix schedule.
+ */
+gbfft_status gbfft_plan_create_nd(gbfft_plan *out, int rank, const int64_t *dims, int64_t batch, int direction,
+                                  int dtype);
+
+/* Shape of a plan: *rank (1 for one-dimensional plans) and dims[0..rank-1]
+ * (dims may be NULL; room for 3). */
+gbfft_status gbfft_plan_dims(gbfft_plan p, int *rank, int64_t *dims);
+
+/*
  * Factorisation-formula front end (the operator vocabulary of Table I, the
  * paper's own input language, Sec. IV-A): DFT(n), I(n), A ⊗ B (or `A kron B`),
  * A · B (or `A * B`, `A . B`), twiddle(N, M) = D^N_M, Permute(N, K) =

@@ -59,7 +59,7 @@ cudaError_t launch_rows(const RowsVariant& v, int direction, const void* in, voi
 
 using namespace gbfft;
 
-enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1, kPlanRagged = 2, kPlanTensorCore = 3 };
+enum PlanKind : int { kPlanSingle = 0, kPlanTwoPass = 1, kPlanRagged = 2, kPlanTensorCore = 3, kPlanND = 4 };
 
 struct gbfft_plan_s {
     int64_t n = 0;
@@ -82,6 +82,12 @@ struct gbfft_plan_s {
     float2* tw_k = nullptr;
     float2* post = nullptr;  // D^N_M in workspace layout
     float2* ws = nullptr;    // workspace z, batch * n complex
+    // multi-dimensional (row-major dims[0] x ... x dims[rank-1]): a single-pass row
+    // transform along the last axis, then in-place column transforms along the others
+    int rank = 1;
+    int64_t dims[3] = {0, 0, 0};
+    const ColsVariant* cv_nd[2] = {nullptr, nullptr};  // axis rank-2, axis rank-3
+    float2* tw_nd[2] = {nullptr, nullptr};
     // ragged batch
     RaggedState* ragged = nullptr;
     // tensor-core split precision (all-radix-16 schedule)
@@ -139,7 +145,7 @@ void free_plan(gbfft_plan p) {
     if (p->umma_b) cudaFree(p->umma_b);
     if (p->tw64) cudaFree(p->tw64);
     if (p->direct_b) cudaFree(p->direct_b);
-    float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws};
+    float2* bufs[] = {p->tw, p->tw_m, p->tw_k, p->post, p->ws, p->tw_nd[0], p->tw_nd[1]};
     for (float2* b : bufs)
         if (b) cudaFree(b);
     if (p->status) cudaFree(p->status);
@@ -148,18 +154,23 @@ void free_plan(gbfft_plan p) {
 
 // Eq. 2 split N = K * M for the two-pass path: M (pass-1 column length) is
 // taken from a preference list; K must also be a registered column length.
+bool split_ok(int64_t k, int64_t m) {
+    // both passes take 16 whole columns per CTA: K (pass 1) and M (pass 2) columns
+    return k % 16 == 0 && m % 16 == 0 && cols_variant_for(k) && cols_variant_for(m);
+}
+
 bool choose_split(int64_t n, int64_t k_req, int64_t* k_out, int64_t* m_out) {
     if (k_req > 0) {
         if (n % k_req != 0) return false;
         const int64_t m = n / k_req;
-        if (!cols_variant_for(k_req) || !cols_variant_for(m)) return false;
+        if (!split_ok(k_req, m)) return false;
         *k_out = k_req;
         *m_out = m;
         return true;
     }
     static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
     for (int64_t m : pref) {
-        if (n % m == 0 && cols_variant_for(m) && cols_variant_for(n / m)) {
+        if (n % m == 0 && split_ok(n / m, m)) {
             *k_out = n / m;
             *m_out = m;
             return true;
@@ -421,6 +432,21 @@ cudaError_t run_device(gbfft_plan p, const void* vin, void* vout, int64_t rows, 
                          p->grid_cap, s);
     if (p->kind == kPlanSingle)
         return launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)rows, p->grid_cap, s, p->status);
+    if (p->kind == kPlanND) {
+        // axis rank-1: rows of length dims[rank-1]; then each other axis as columns, in place
+        const int64_t last = p->dims[p->rank - 1];
+        const int64_t per = p->n / last;  // rows per array
+        cudaError_t e = launch_rows(*p->rv, p->direction, in, out, p->tw, (long long)(rows * per), p->grid_cap, s,
+                                    p->status);
+        int64_t inner = last;             // elements after the axis being transformed
+        for (int ax = p->rank - 2, c = 0; e == cudaSuccess && ax >= 0; --ax, ++c) {
+            const int64_t outer = p->n / (p->dims[ax] * inner);  // arrays of (dims[ax] x inner) per item
+            e = launch_cols(*p->cv_nd[c], 2, p->direction, out, out, p->tw_nd[c], nullptr,
+                            (long long)(rows * outer), (int)inner, s);
+            inner *= p->dims[ax];
+        }
+        return e;
+    }
     cudaError_t e = launch_cols(*p->cv_m, 1, p->direction, in, p->ws, p->tw_m, p->post, (long long)rows,
                                 (int)p->k_outer, s);
     if (e != cudaSuccess) return e;
@@ -472,6 +498,78 @@ gbfft_status gbfft_plan_create_twopass(gbfft_plan* out, int64_t n, int64_t batch
         k_outer = kk;
     }
     return create(out, n, batch, direction, dtype, -1, k_outer);
+}
+
+// Multi-dimensional plan: DFT_{d0} (x) ... (x) DFT_{d(r-1)} on row-major arrays
+// (the Kronecker product of Table I applied to whole transforms): the last
+// axis by a single-pass row kernel, every other axis by the column kernel of
+// Eq. 2's second pass (length-d transforms down `inner` columns, in place).
+gbfft_status gbfft_plan_create_nd(gbfft_plan* out, int rank, const int64_t* dims, int64_t batch, int direction,
+                                  int dtype) {
+    if (!out) return GBFFT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (rank < 1 || rank > 3 || !dims || batch < 0) return GBFFT_ERR_INVALID_ARG;
+    if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
+    if (dtype != GBFFT_C2C_F32) return GBFFT_ERR_INVALID_ARG;
+    for (int i = 0; i < rank; ++i)
+        if (dims[i] < 1 || dims[i] > ((int64_t)1 << 20)) return GBFFT_ERR_INVALID_ARG;
+    if (rank == 1) return create(out, dims[0], batch, direction, dtype, -1, 0);
+    const int64_t last = dims[rank - 1];
+    const RowsVariant* cands[kMaxVariantsPerSize];
+    if (rows_variants_for(last, cands, kMaxVariantsPerSize) == 0) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    if (last % 16 != 0) return GBFFT_ERR_UNSUPPORTED_SIZE;  // column kernels take 16 columns per CTA
+    const ColsVariant* cv[2] = {nullptr, nullptr};
+    for (int ax = rank - 2, c = 0; ax >= 0; --ax, ++c) {
+        cv[c] = cols_variant_for(dims[ax]);
+        if (!cv[c]) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    }
+    int64_t total = 1;
+    for (int i = 0; i < rank; ++i) total *= dims[i];
+    if (total > ((int64_t)1 << 31)) return GBFFT_ERR_INVALID_ARG;
+    gbfft_plan p = new (std::nothrow) gbfft_plan_s();
+    if (!p) return GBFFT_ERR_OOM;
+    p->kind = kPlanND;
+    p->rank = rank;
+    for (int i = 0; i < rank; ++i) p->dims[i] = dims[i];
+    p->n = total;
+    p->batch = batch;
+    p->direction = direction;
+    p->dtype = dtype;
+    p->variant = 0;
+    p->rv = cands[0];
+    gbfft_status st = GBFFT_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
+        cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        st = GBFFT_ERR_CUDA;
+    }
+    if (st == GBFFT_OK && prepare_rows(*p->rv) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && (p->rv->kind == kRowsPersistent || p->rv->kind == kRowsTma)) {
+        p->grid_cap = persistent_grid(*p->rv);
+        if (p->grid_cap <= 0) st = GBFFT_ERR_CUDA;
+    }
+    if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw, last, p->rv->radix, p->rv->nstages);
+    for (int c = 0; st == GBFFT_OK && c < rank - 1; ++c) {
+        p->cv_nd[c] = cv[c];
+        if (prepare_cols(*cv[c]) != cudaSuccess) st = GBFFT_ERR_CUDA;
+        if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw_nd[c], cv[c]->len, cv[c]->radix, cv[c]->nstages);
+    }
+    if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st != GBFFT_OK) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return GBFFT_OK;
+}
+
+gbfft_status gbfft_plan_dims(gbfft_plan p, int* rank, int64_t* dims) {
+    if (!p) return GBFFT_ERR_INVALID_ARG;
+    const int r = p->kind == kPlanND ? p->rank : 1;
+    if (rank) *rank = r;
+    if (dims)
+        for (int i = 0; i < r; ++i) dims[i] = p->kind == kPlanND ? p->dims[i] : p->n;
+    return GBFFT_OK;
 }
 
 // A plan that follows a factorisation formula as literally as the compiled
@@ -533,6 +631,7 @@ gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_s
     gbfft_status st = check_io(in, out, bytes);
     if (st != GBFFT_OK) return st;
     cudaError_t e = run_device(p, in, out, p->batch, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) cudaGetLastError();  // a failed launch must not surface in later calls
     return e == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
@@ -596,6 +695,7 @@ gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_ou
         if (used < gbfft_plan_s::kRing) ++used;
     }
     for (int b = 0; ok && b < used; ++b) ok = cudaStreamWaitEvent(su, p->ev_out[b], 0) == cudaSuccess;
+    if (!ok) cudaGetLastError();
     return ok ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
@@ -618,7 +718,7 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
         rad[ns++] = (int)p->n;  // the direct DFT: one dense stage of radix N
     } else if (p->kind == kPlanTensorCore) {
         for (int i = 0; i < p->tcv->nstages; ++i) rad[ns++] = 16;
-    } else if (p->kind == kPlanSingle) {
+    } else if (p->kind == kPlanSingle || p->kind == kPlanND) {  // ND: the last axis' row schedule
         for (int i = 0; i < p->rv->nstages; ++i) rad[ns++] = p->rv->radix[i];
     } else {
         for (int i = 0; i < p->cv_m->nstages; ++i) rad[ns++] = p->cv_m->radix[i];

@@ -144,7 +144,8 @@ gbfft_status gbfft_autotune(int64_t n, int64_t batch, int direction, int dtype, 
         for (int v = 0; v < nv; ++v) cands.push_back({v, 0});
         static const int64_t lens[] = {32, 48, 64, 80, 96, 112, 128, 256, 512};
         for (int64_t k : lens)
-            if (n % k == 0 && cols_variant_for(k) && cols_variant_for(n / k)) cands.push_back({-1, k});
+            if (n % k == 0 && (n / k) % 16 == 0 && cols_variant_for(k) && cols_variant_for(n / k))
+                cands.push_back({-1, k});
     } else if (dtype == GBFFT_C2C_F64) {
         const int nv = rows_variants_f64_for(n, nullptr, 0);
         for (int v = 0; v < nv; ++v) cands.push_back({v, 0});

@@ -26,6 +26,8 @@ inline ColsVariant make_cols_variant() {
 #define GBFFT_COLS(LEN, E, C, ...) make_cols_variant<LEN, E, C, __VA_ARGS__>()
 
 static const ColsVariant kCols[] = {
+    GBFFT_COLS(8, 4, 16, 2, 4),
+    GBFFT_COLS(16, 4, 16, 4, 4),
     GBFFT_COLS(32, 8, 16, 4, 8),
     GBFFT_COLS(48, 12, 16, 3, 4, 4),
     GBFFT_COLS(64, 8, 16, 8, 8),

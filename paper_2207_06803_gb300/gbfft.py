@@ -80,6 +80,8 @@ PROTOTYPES = {
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
     "gbfft_ragged_queue_order": (_c_int, [_c_vp]),
     "gbfft_ragged_schedule": (_c_int, [_c_vp, _c_i64, _c_intp]),
+    "gbfft_plan_create_nd": (_c_int, [ctypes.POINTER(_c_vp), _c_int, _c_i64p, _c_i64, _c_int, _c_int]),
+    "gbfft_plan_dims": (_c_int, [_c_vp, _c_intp, _c_i64p]),
     "gbfft_formula_check": (_c_int, [ctypes.c_char_p, _c_i64p, _c_intp, _c_int, _c_intp, _c_i64p, ctypes.c_char_p,
                                      ctypes.c_size_t]),
     "gbfft_plan_create_formula": (_c_int, [ctypes.POINTER(_c_vp), ctypes.c_char_p, _c_i64, _c_int, _c_int, _c_intp]),
@@ -307,6 +309,21 @@ def gbfft_ragged_tile_split(plan: int, n: int) -> int:
     return int(lib().gbfft_ragged_tile_split(plan, n))
 
 
+def gbfft_plan_create_nd(dims, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32) -> int:
+    d = (ctypes.c_int64 * max(3, len(dims)))(*[int(v) for v in dims])
+    h = ctypes.c_void_p()
+    _check(lib().gbfft_plan_create_nd(ctypes.byref(h), len(dims), d, batch, direction, dtype),
+           "gbfft_plan_create_nd")
+    return h.value
+
+
+def gbfft_plan_dims(plan: int) -> list[int]:
+    r = ctypes.c_int()
+    d = (ctypes.c_int64 * 3)()
+    _check(lib().gbfft_plan_dims(plan, ctypes.byref(r), d), "gbfft_plan_dims")
+    return list(d[: r.value])
+
+
 def gbfft_formula_check(formula: str) -> dict:
     """Check a Table I factorisation formula; {'n', 'k_outer', 'leaves'} or GbfftError (message in .args)."""
     n, k = ctypes.c_int64(), ctypes.c_int64()
@@ -493,11 +510,23 @@ class Server:
             pass
 
 
-class Plan:
-    """Owning wrapper: ``with Plan(n, batch) as p: p.execute(x, y, stream)``."""
+def _prod(dims) -> int:
+    out = 1
+    for v in dims:
+        out *= int(v)
+    return out
 
-    def __init__(self, n: int, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32,
+
+class Plan:
+    """Owning wrapper: ``with Plan(n, batch) as p: p.execute(x, y, stream)``; ``n`` may be a shape
+    tuple (dims[0], ..., dims[rank-1]) for a multi-dimensional transform."""
+
+    def __init__(self, n, batch: int, direction: int = GBFFT_FORWARD, dtype: int = GBFFT_C2C_F32,
                  variant: int | None = None, k_outer: int | None = None):
+        if isinstance(n, (tuple, list)):
+            self.handle = gbfft_plan_create_nd(n, batch, direction, dtype)
+            self.n, self.batch, self.direction = _prod(n), batch, direction
+            return
         if k_outer is not None:
             self.handle = gbfft_plan_create_twopass(n, batch, direction, dtype, k_outer)
         elif variant is None:
