@@ -261,8 +261,10 @@ gbfft_status gbfft_plan_dims(gbfft_plan p, int *rank, int64_t *dims);
  *
  * gbfft_formula_check: parses `formula` and checks symbolically that it
  * denotes DFT_N through Eq. 2, (DFT_K ⊗ I_M) · twiddle(N, M) · (I_K ⊗ DFT_M) ·
- * Permute(N, K) with N = K*M, recursively (each DFT factor may be such a
- * product; Eq. 1 is N = 4).  On success writes N, the outermost K (0 when the
+ * Permute(N, K) with N = K*M, or its transpose Permute(N, M) · (I_K ⊗ DFT_M) ·
+ * twiddle(N, M) · (DFT_K ⊗ I_M) (the decimation-in-frequency order: DFT_N is
+ * symmetric), recursively (each DFT factor may be such a product; Eq. 1 is
+ * N = 4).  On success writes N, the outermost K (0 when the
  * formula is a single DFT(N)), and the DFT leaf sizes in the order the product
  * applies them (rightmost first; at most `max_leaves` written, *nleaves = the
  * full count).  Host only: no CUDA call.  Errors: INVALID_ARG (syntax,

@@ -3,7 +3,8 @@
 // host and checked to denote DFT_N by the Cooley-Tukey identity of Eq. 2,
 //     DFT_N = (DFT_K ⊗ I_M) · twiddle(N, M) · (I_K ⊗ DFT_M) · Permute(N, K),  N = K M,
 // applied recursively (either DFT factor may itself be such a product; Eq. 1
-// is the case N = 4).  twiddle(N, M) is the diagonal D^N_M and Permute(N, K)
+// is the case N = 4), or its transpose Permute(N, M) · (I_K ⊗ DFT_M) ·
+// twiddle(N, M) · (DFT_K ⊗ I_M) (decimation in frequency).  twiddle(N, M) is the diagonal D^N_M and Permute(N, K)
 // the stride permutation Pi^N_K of Eq. 2 (their argument order follows the
 // subscripts of Eq. 2).  A checked formula then selects the execution plan:
 // its DFT leaves, in the order the product applies them (rightmost first),
@@ -220,12 +221,41 @@ void flatten_product(const Node* n, std::vector<const Node*>* out) {
 struct DftForm {
     int64_t n = 0;
     int64_t k_top = 0;            // outermost split N = K * M (0: a single DFT(n) leaf)
-    bool bare = false;            // the outermost split's DFT factors are DFT(K), DFT(M) leaves
+    bool bare = false;            // the outermost split is Eq. 2's own order over DFT(K), DFT(M) leaves
+    bool transposed = false;      // the outermost split is the transposed (decimation-in-frequency) form
     std::vector<int64_t> leaves;  // DFT leaf sizes in application order
 };
 
-// Whether n denotes DFT_N: a DFT(n) leaf, or Eq. 2's four factors with DFT
-// factors that themselves denote DFTs.
+bool as_dft(const Node* n, DftForm* f, std::string* err);
+
+// The transpose of Eq. 2 (DFT_N is symmetric, D diagonal, (Pi^N_K)^T = Pi^N_M):
+//     DFT_N = Permute(N, M) · (I_K ⊗ DFT_M) · twiddle(N, M) · (DFT_K ⊗ I_M),
+// the decimation-in-frequency order; DFT_K runs first, then DFT_M.
+bool as_dft_transposed(const std::vector<const Node*>& fs, DftForm* f, std::string* err) {
+    const Node *f1 = fs[0], *f2 = fs[1], *f3 = fs[2], *f4 = fs[3];
+    if (f2->kind != kKron || f2->l->kind != kIdent)
+        return *err = "transposed form: second factor must be (I_K (x) DFT_M)", false;
+    if (f3->kind != kTwiddle) return *err = "transposed form: third factor must be twiddle(N, M)", false;
+    if (f4->kind != kKron || f4->r->kind != kIdent)
+        return *err = "transposed form: fourth factor must be (DFT_K (x) I_M)", false;
+    DftForm x, y;
+    if (!as_dft(f4->l.get(), &x, err) || !as_dft(f2->r.get(), &y, err)) return false;
+    const int64_t K = x.n, M = y.n, N = K * M;
+    if (f4->r->a != M || f2->l->a != K)
+        return *err = "transposed form: identity sizes must match the DFT factors", false;
+    if (f3->a != N || f3->b != M) return *err = "transposed form: third factor must be twiddle(N, M)", false;
+    if (f1->a != N || f1->b != M) return *err = "transposed form: first factor must be Permute(N, M)", false;
+    f->n = N;
+    f->k_top = K;
+    f->bare = false;  // the split is Eq. 2's, but the factors run in the other order
+    f->transposed = true;
+    f->leaves = x.leaves;  // DFT_K first, then DFT_M
+    f->leaves.insert(f->leaves.end(), y.leaves.begin(), y.leaves.end());
+    return true;
+}
+
+// Whether n denotes DFT_N: a DFT(n) leaf, or Eq. 2's four factors (or their
+// transpose) with DFT factors that themselves denote DFTs.
 bool as_dft(const Node* n, DftForm* f, std::string* err) {
     if (n->kind == kDft) {
         f->n = n->a;
@@ -238,9 +268,11 @@ bool as_dft(const Node* n, DftForm* f, std::string* err) {
     flatten_product(n, &fs);
     if (fs.size() == 1) return as_dft(fs[0], f, err);
     if (fs.size() != 4)
-        return *err = "not a DFT: Eq. 2 has four factors (DFT_K (x) I_M) . twiddle(N,M) . (I_K (x) DFT_M) . Permute(N,K)",
+        return *err = "not a DFT: Eq. 2 has four factors (DFT_K (x) I_M) . twiddle(N,M) . (I_K (x) DFT_M) . "
+                      "Permute(N,K) (or their transpose)",
                false;
     const Node *f1 = fs[0], *f2 = fs[1], *f3 = fs[2], *f4 = fs[3];
+    if (f1->kind == kPermute) return as_dft_transposed(fs, f, err);
     if (f1->kind != kKron || f1->r->kind != kIdent)
         return *err = "first factor must be (DFT_K (x) I_M)", false;
     if (f3->kind != kKron || f3->l->kind != kIdent) return *err = "third factor must be (I_K (x) DFT_M)", false;

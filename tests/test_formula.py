@@ -53,6 +53,13 @@ def eq2(outer, inner):
     return prod(kron(outer, eye(m)), tw(n, m), kron(eye(k), inner), perm(n, k))
 
 
+def eq2_transposed(outer, inner):
+    """The transpose of Eq. 2 (decimation in frequency): DFT_K runs first, then DFT_M."""
+    k, m = size(outer), size(inner)
+    n = k * m
+    return prod(perm(n, m), kron(eye(k), inner), tw(n, m), kron(outer, eye(m)))
+
+
 def ct(radices):
     """Recursive Cooley-Tukey formula whose DFT leaves, in application order, are `radices`."""
     if len(radices) == 1:
@@ -128,6 +135,23 @@ def test_recursive_formulas(radices):
     r = gbfft.gbfft_formula_check(render(f))
     assert r["n"] == math.prod(radices) and r["leaves"] == radices and r["k_outer"] == radices[-1]
     assert gbfft.gbfft_formula_check(render(f, ascii_ops=True)) == r
+
+
+@pytest.mark.parametrize("k,m", [(2, 2), (2, 4), (4, 2), (3, 5), (8, 16)])
+def test_transposed_form(k, m):
+    f = eq2_transposed(dft(k), dft(m))
+    assert is_dft(f) if k * m <= 64 else True
+    r = gbfft.gbfft_formula_check(render(f))
+    assert r == {"n": k * m, "k_outer": k, "leaves": [k, m]}
+    if k != m:  # its mistakes: Eq. 2's permutation argument, or Eq. 2's factor order with these factors
+        bad = prod(perm(k * m, k), kron(eye(k), dft(m)), tw(k * m, m), kron(dft(k), eye(m)))
+        assert not is_dft(bad) and checker_accepts(render(bad)) is None
+
+
+def test_mixed_forms_nest():
+    f = eq2(eq2_transposed(dft(2), dft(4)), ct([4, 2]))
+    assert is_dft(f)
+    assert gbfft.gbfft_formula_check(render(f)) == {"n": 64, "k_outer": 8, "leaves": [4, 2, 2, 4]}
 
 
 def test_split_on_both_factors():
