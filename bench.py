@@ -244,9 +244,15 @@ def cpu_baseline(flat, target_s: float = 12.0):
     pts = calibrate_oracle(flat, cores, target_s)
     dt = oracle_sweep_once(flat, pts, cores)
     nbytes = 16.0 * pts * len(SWEEP) * 2
+    # the paper's own setting is one thread: the same oracle on one core, on a smaller sample
+    pts1 = calibrate_oracle(flat, 1, 3.0)
+    dt1 = oracle_sweep_once(flat, pts1, 1)
+    single = {"value": 16.0 * pts1 * len(SWEEP) * 2 / dt1 / 1e9, "unit": UNIT, "cores": 1,
+              "sample": f"{pts1} points per (N, direction), 1 thread, {dt1:.1f} s"}
     return {"value": nbytes / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": (f"FP64 recursive radix-2 oracle, {pts} points per (N, direction) of the sweep "
-                       f"({len(SWEEP)} sizes x 2 directions), {cores} threads over rows, {dt:.1f} s")}
+                       f"({len(SWEEP)} sizes x 2 directions), {cores} threads over rows, {dt:.1f} s"),
+            "single_core": single}
 
 
 def run_reference(args):
