@@ -56,11 +56,19 @@ struct DirectGeom {
     static_assert(N % 8 == 0 && BLK * K <= 256, "direct DFT: N a multiple of 8, tile columns <= 256");
 };
 
+// 32 bytes (8 floats) from a 32-byte-aligned global address in one request.
+__device__ __forceinline__ void ld_global_v8(const float4* p, float (&w)[8]) {
+    asm volatile("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(w[0]), "=f"(w[1]), "=f"(w[2]), "=f"(w[3]), "=f"(w[4]), "=f"(w[5]), "=f"(w[6]), "=f"(w[7])
+                 : "l"(p));
+}
+
 __device__ __forceinline__ uint32_t k_offset(int row, int kg, int sbo) {
     return (uint32_t)((row >> 3) * sbo + kg * 128 + (row & 7) * 16);
 }
 
-template <int N, int S, int PREC>
+// V8: the input is 32-byte aligned (every chunk then is) and is read with 32-byte loads.
+template <int N, int S, int PREC, bool V8>
 __global__ void __launch_bounds__(DirectGeom<N>::ROWS) k_dft_direct_umma(const float2* in, float2* out,
                                                                          const uint4* __restrict__ bmat,
                                                                          long long batch, int* status) {
@@ -117,14 +125,28 @@ __global__ void __launch_bounds__(DirectGeom<N>::ROWS) k_dft_direct_umma(const f
 #pragma unroll
                 for (int hh = 0; hh < H; ++hh) {
                     const int j = q % LPR + LPR * hh;
+                    if constexpr (V8) {
+                        // 32-byte loads: each request covers whole sectors
 #pragma unroll
-                    for (int h = 0; h < 4; ++h) {
-                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (j < CPR && row < nvalid) v = src[(row * N + 8 * j) / 2 + h];
-                        re[hh][2 * h] = v.x;
-                        im[hh][2 * h] = v.y;
-                        re[hh][2 * h + 1] = v.z;
-                        im[hh][2 * h + 1] = v.w;
+                        for (int h = 0; h < 2; ++h) {
+                            float w[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                            if (j < CPR && row < nvalid) ld_global_v8(src + (row * N + 8 * j) / 2 + 2 * h, w);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                re[hh][4 * h + e] = w[2 * e];
+                                im[hh][4 * h + e] = w[2 * e + 1];
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (j < CPR && row < nvalid) v = src[(row * N + 8 * j) / 2 + h];
+                            re[hh][2 * h] = v.x;
+                            im[hh][2 * h] = v.y;
+                            re[hh][2 * h + 1] = v.z;
+                            im[hh][2 * h + 1] = v.w;
+                        }
                     }
 #pragma unroll
                     for (int e = 0; e < 8; ++e) m = fmaxf(m, fmaxf(fabsf(re[hh][e]), fabsf(im[hh][e])));
@@ -272,10 +294,14 @@ DirectVariant make_direct_variant() {
     v.smem = DirectGeom<N>::SMEM;
     v.bmat_bytes = DirectGeom<N>::B_BYTES;
     v.tmem_cols = (int)DirectGeom<N>::COLS;
-    v.k[0][0] = (const void*)&k_dft_direct_umma<N, -1, 0>;
-    v.k[0][1] = (const void*)&k_dft_direct_umma<N, +1, 0>;
-    v.k[1][0] = (const void*)&k_dft_direct_umma<N, -1, 1>;
-    v.k[1][1] = (const void*)&k_dft_direct_umma<N, +1, 1>;
+    v.k[0][0] = (const void*)&k_dft_direct_umma<N, -1, 0, false>;
+    v.k[0][1] = (const void*)&k_dft_direct_umma<N, +1, 0, false>;
+    v.k[1][0] = (const void*)&k_dft_direct_umma<N, -1, 1, false>;
+    v.k[1][1] = (const void*)&k_dft_direct_umma<N, +1, 1, false>;
+    v.k32[0][0] = (const void*)&k_dft_direct_umma<N, -1, 0, true>;
+    v.k32[0][1] = (const void*)&k_dft_direct_umma<N, +1, 0, true>;
+    v.k32[1][0] = (const void*)&k_dft_direct_umma<N, -1, 1, true>;
+    v.k32[1][1] = (const void*)&k_dft_direct_umma<N, +1, 1, true>;
     return v;
 }
 
@@ -296,6 +322,8 @@ cudaError_t prepare_direct(const DirectVariant& v) {
     for (int p = 0; p < 2; ++p)
         for (int d = 0; d < 2; ++d) {
             cudaError_t e = cudaFuncSetAttribute(v.k[p][d], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(v.k32[p][d], cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -332,7 +360,8 @@ cudaError_t launch_direct(const DirectVariant& v, int prec, int direction, const
     long long blocks = (batch + v.rows - 1) / v.rows;
     if (grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
     void* args[] = {(void*)&in, (void*)&out, (void*)&bmat, (void*)&batch, (void*)&status};
-    const void* fn = v.k[prec][direction == GBFFT_FORWARD ? 0 : 1];
+    const bool a32 = ((uintptr_t)in & 31u) == 0;  // 32-byte loads need a 32-byte-aligned input
+    const void* fn = (a32 ? v.k32 : v.k)[prec][direction == GBFFT_FORWARD ? 0 : 1];
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.tpb), args, (size_t)v.smem, s);
 }
 

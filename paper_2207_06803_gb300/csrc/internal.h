@@ -95,7 +95,8 @@ cudaError_t launch_umma(const UmmaVariant& v, int prec, int direction, const flo
 // half-precision matrix product per 128 transforms; N = 8, 16, ..., 64.
 struct DirectVariant {
     int n, rows, tpb, smem, bmat_bytes, tmem_cols;
-    const void* k[2][2];  // [prec][dir]
+    const void* k[2][2];    // [prec][dir], 16-byte loads
+    const void* k32[2][2];  // the same with 32-byte loads, for 32-byte-aligned inputs
 };
 const DirectVariant* direct_variant_for(int64_t n);
 cudaError_t prepare_direct(const DirectVariant& v);

@@ -168,6 +168,28 @@ def test_direct_dft_engine_every_size(direction):
             assert err.max() <= 1e-6 * math.log2(n), (n, dist, err.max())
 
 
+def test_direct_dft_load_paths_agree():
+    """32-byte-aligned inputs take 32-byte loads, 16-byte-aligned ones 16-byte loads: same bits."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    for n in (8, 24, 64):
+        batch = 300
+        x = synth.uniform_batch(SEED, n, batch)
+        base = torch.zeros(2 * n * batch + 8, device="cuda")
+        a = base[:2 * n * batch]                   # 256-byte aligned
+        b = base[4:4 + 2 * n * batch]              # 16 bytes further: 16- but not 32-byte aligned
+        assert a.data_ptr() % 32 == 0 and b.data_ptr() % 32 == 16
+        outs = []
+        for buf in (a, b):
+            buf.copy_(torch.from_numpy(x.view(np.float32).reshape(-1)).cuda())
+            out = torch.empty(2 * n * batch, device="cuda")
+            with gbfft.Plan(n, batch, -1, dtype=1, variant=2) as p:
+                p.execute(buf, out)
+            torch.cuda.synchronize()
+            outs.append(out)
+        assert torch.equal(outs[0], outs[1]), n
+
+
 def test_direct_dft_in_place_default_engine_and_bf16_rejected():
     import torch
     from paper_2207_06803_gb300 import gbfft
