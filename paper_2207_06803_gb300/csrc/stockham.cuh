@@ -90,6 +90,39 @@ struct IndexedIO {
     __device__ __forceinline__ void st(int t, int n, C v) const { out[off[t] + n] = v; }
 };
 
+// Stage twiddles w^q, q = 1..15, of a radix-16 butterfly with index k from
+// its stage block W[(q-1)*L + k]: the entries for q = 1, 2, 4, 8 are read, the
+// other powers formed as products of those (at most three multiplications
+// deep, each product of table values that are themselves correctly rounded).
+template <class C>
+__device__ __forceinline__ void twiddle_powers16(const C* __restrict__ blk, int L, int k, C (&w)[16]) {
+    const C w1 = __ldg(&blk[k]), w2 = __ldg(&blk[L + k]);
+    const C w4 = __ldg(&blk[3 * L + k]), w8 = __ldg(&blk[7 * L + k]);
+    w[1] = w1;
+    w[2] = w2;
+    w[3] = cmul(w1, w2);
+    w[4] = w4;
+    w[5] = cmul(w1, w4);
+    w[6] = cmul(w2, w4);
+    w[7] = cmul(w[3], w4);
+    w[8] = w8;
+#pragma unroll
+    for (int q = 9; q < 16; ++q) w[q] = cmul(w[q - 8], w8);
+}
+
+// The same for a radix-8 butterfly: q = 1, 2, 4 read, q = 3, 5, 6, 7 by products.
+template <class C>
+__device__ __forceinline__ void twiddle_powers8(const C* __restrict__ blk, int L, int k, C (&w)[8]) {
+    const C w1 = __ldg(&blk[k]), w2 = __ldg(&blk[L + k]), w4 = __ldg(&blk[3 * L + k]);
+    w[1] = w1;
+    w[2] = w2;
+    w[3] = cmul(w1, w2);
+    w[4] = w4;
+    w[5] = cmul(w1, w4);
+    w[6] = cmul(w2, w4);
+    w[7] = cmul(w[3], w4);
+}
+
 // Butterflies of radix R per thread when TPB threads share the T*N/R
 // butterflies of a stage (the last round may leave threads idle).
 template <int N, int T, int TPB, int R>
@@ -154,24 +187,17 @@ __device__ __forceinline__ void run_stages_t(C (&v)[E], const IO& io, C* sm, con
             const int B = tid + u * TPB;
             const int k = (B % NR) % L;
             if constexpr (R == 16 && sizeof(C) == sizeof(float2)) {
-                // FP32: w_q = w^q for q = 1, 2, 4, 8 from the table, the other powers as products of
-                // those (at most three multiplications deep): 4 table reads per butterfly instead of
-                // 15 takes the twiddle loads off the critical path of the large sizes (N = 2048: 96 ->
-                // 99.7 %, N = 4096: 95 -> 98.5 % of the copy rate).  The FP64 path keeps the table
-                // reads: it is bound by the FP64 pipe, where the products would cost more.
-                const C w1 = __ldg(&tw[TWO + k]), w2 = __ldg(&tw[TWO + L + k]);
-                const C w4 = __ldg(&tw[TWO + 3 * L + k]), w8 = __ldg(&tw[TWO + 7 * L + k]);
+                // FP32: 4 table reads per butterfly instead of 15 takes the twiddle loads off the
+                // critical path of the large sizes (N = 2048: 96 -> 99.7 %, N = 4096: 95 -> 98.5 % of
+                // the copy rate).  The FP64 path keeps the table reads: it is bound by the FP64 pipe,
+                // where the products would cost more.
                 C w[16];
-                w[1] = w1;
-                w[2] = w2;
-                w[3] = cmul(w1, w2);
-                w[4] = w4;
-                w[5] = cmul(w1, w4);
-                w[6] = cmul(w2, w4);
-                w[7] = cmul(w[3], w4);
-                w[8] = w8;
+                twiddle_powers16(tw + TWO, L, k, w);
 #pragma unroll
-                for (int q = 9; q < 16; ++q) w[q] = cmul(w[q - 8], w8);
+                for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], w[q]);
+            } else if constexpr (R == 8 && sizeof(C) == sizeof(float2)) {
+                C w[8];
+                twiddle_powers8(tw + TWO, L, k, w);
 #pragma unroll
                 for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], w[q]);
             } else {

@@ -83,9 +83,12 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
         } else {
             x[q] = sh.xbuf[spad<PS>(t * N + n)];
         }
-        if constexpr (L > 1) {
-            if (q > 0) x[q] = twiddle<S>(x[q], __ldg(&tw[(q - 1) * L + k]));
-        }
+    }
+    if constexpr (L > 1) {
+        float2 w[16];
+        twiddle_powers16(tw, L, k, w);  // four table reads, the other powers by products
+#pragma unroll
+        for (int q = 1; q < 16; ++q) x[q] = twiddle<S>(x[q], w[q]);
     }
     float inv_sc = 1.f;
     if constexpr (PREC == 0) {
