@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "codelets.cuh"
+#include "stockham.cuh"
 #include "gbfft.h"
 
 namespace gbfft {
@@ -129,9 +130,21 @@ __device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const
             const int B = min(tid + u * kRaggedThreads, last);
             const int t = rdiv(B, st.mag_nr), j = B - t * nr;
             const int k = j - rdiv(j, st.mag_l) * L;
-            const float2* w = tw + st.tw + k;
+            const float2* w = tw + st.tw;
+            if constexpr (R == 16) {  // four table reads, the other powers by products
+                float2 p[16];
+                twiddle_powers16(w, L, k, p);
 #pragma unroll
-            for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], __ldg(w + (q - 1) * L));
+                for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], p[q]);
+            } else if constexpr (R == 8) {
+                float2 p[8];
+                twiddle_powers8(w, L, k, p);
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], p[q]);
+            } else {
+#pragma unroll
+                for (int q = 1; q < R; ++q) v[u * R + q] = twiddle<S>(v[u * R + q], __ldg(w + (q - 1) * L + k));
+            }
         }
     }
 #pragma unroll
