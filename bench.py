@@ -447,7 +447,9 @@ def other_configs(args):
             out[name] = {"error": f"{type(e).__name__}: {e}"}
             continue
         if name == "twopass":
-            out[name] = {n: round(v["alg_gbs"], 1) for n, v in r["per_size"].items()}
+            out[name] = {n: {"two_pass_gbs": round(v["alg_gbs"], 1),
+                             **({"cluster_gbs": round(v["cluster_gbs"], 1)} if "cluster_gbs" in v else {})}
+                         for n, v in r["per_size"].items()}
         elif name == "tc":
             out[name] = {k: {"gbs": round(v["gbs"], 1), "vs_fp32": round(v["vs_fp32"], 3),
                              "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for k, v in r["results"].items()}
@@ -533,14 +535,25 @@ def run_twopass(args):
     stream = torch.cuda.current_stream()
     peak, src = _peak()
     rows = {}
-    for n in (5120, 6144, 7168, 8192, 10240, 12288, 14336, 16384, 65536):
-        with gbfft.Plan(n, TOTAL // n, -1) as p:
+    for n in (5120, 6144, 7168, 8192, 10240, 12288, 14336, 16384, 20480, 24576, 28672, 32768, 65536):
+        batch = TOTAL // n
+        res = {}
+        with gbfft.Plan(n, batch, -1, k_outer=0) as p:  # Eq. 2 as two passes (two HBM round trips): the default
             info = p.info()
             ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
-        alg = BYTES_PER_CALL / (ms * 1e-3) / 1e9
-        rows[str(n)] = {"k_outer": info["k_outer"], "m_inner": info["m_inner"], "ms": ms, "alg_gbs": alg,
-                        "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak}
-    return {"config": "twopass", "metric": "two-pass Eq. 2 c2c GB/s (16 B/point algorithmic)",
+        alg = 16.0 * n * batch / (ms * 1e-3) / 1e9
+        res.update({"k_outer": info["k_outer"], "m_inner": info["m_inner"], "ms": ms, "alg_gbs": alg,
+                    "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak})
+        if gbfft.gbfft_num_variants(n) > 0:  # one pass on a thread-block cluster (variant 0)
+            with gbfft.Plan(n, batch, -1, variant=0) as p:
+                rad = p.info()["radices"]
+                ms1 = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+            alg1 = 16.0 * n * batch / (ms1 * 1e-3) / 1e9
+            res.update({"cluster_radices": rad, "cluster_ms": ms1, "cluster_gbs": alg1,
+                        "cluster_frac_of_hbm": alg1 / peak, "cluster_vs_two_pass": ms / ms1})
+        rows[str(n)] = res
+    return {"config": "twopass", "metric": "N > 4096: one pass on a thread-block cluster and Eq. 2 as two passes, "
+                                           "c2c GB/s (16 B/point algorithmic)",
             "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_size": rows}
 
 

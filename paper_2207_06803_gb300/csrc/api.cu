@@ -29,6 +29,11 @@ int rows_variants_for(int64_t n, const RowsVariant** out, int max_out) {
     return found;
 }
 
+int onepass_variants_for(int64_t n, const RowsVariant** out, int max_out) {
+    const int nr = rows_variants_for(n, out, max_out);
+    return nr > 0 ? nr : cluster_variants_for(n, out, max_out);
+}
+
 int persistent_grid(const RowsVariant& v) {
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -50,6 +55,7 @@ cudaError_t launch_rows(const RowsVariant& v, int direction, const void* in, voi
     if (batch <= 0) return cudaSuccess;
     long long blocks = (batch + v.rows - 1) / v.rows;
     if ((v.kind == kRowsPersistent || v.kind == kRowsTma) && grid_cap > 0 && blocks > grid_cap) blocks = grid_cap;
+    if (v.kind == kRowsCluster) blocks = batch * v.radix[v.nstages - 1];  // one row per cluster of K CTAs
     void* args[] = {(void*)&in, (void*)&out, (void*)&tw, (void*)&batch, (void*)&status};
     const void* fn = direction == GBFFT_FORWARD ? v.kfwd : v.kinv;
     return cudaLaunchKernel(fn, dim3((unsigned)blocks), dim3(v.tpb), args, (size_t)v.smem, stream);
@@ -333,7 +339,7 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
                 int64_t kk, mm;
                 if (choose_split(n, wk, &kk, &mm)) k_outer = wk;
             } else if (wv >= 0) {
-                const int limit = dtype == GBFFT_C2C_F32   ? rows_variants_for(n, nullptr, 0)
+                const int limit = dtype == GBFFT_C2C_F32   ? onepass_variants_for(n, nullptr, 0)
                                   : dtype == GBFFT_C2C_F64 ? rows_variants_f64_for(n, nullptr, 0)
                                                            : 3;
                 if (wv < limit) variant = wv;
@@ -352,9 +358,13 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     }
 
     const RowsVariant* cands[kMaxVariantsPerSize];
-    const int nc = rows_variants_for(n, cands, kMaxVariantsPerSize);
+    const int nc = onepass_variants_for(n, cands, kMaxVariantsPerSize);
     int64_t kk = 0, mm = 0;
-    const bool two_pass = k_outer > 0 || (nc == 0 && variant < 0);
+    // Above 4096 the default is Eq. 2 as two passes: the one-pass cluster kernels (the row kept
+    // on chip, exchanged through distributed shared memory) measured slower on GB300 and are
+    // chosen only when forced or by the autotuner, or when no split exists.
+    const bool cluster_only = nc > 0 && rows_variants_for(n, nullptr, 0) == 0;
+    const bool two_pass = k_outer > 0 || (variant < 0 && (nc == 0 || (cluster_only && choose_split(n, 0, &kk, &mm))));
     if (two_pass) {
         if (!choose_split(n, k_outer, &kk, &mm)) return k_outer > 0 ? GBFFT_ERR_NOT_FOUND : GBFFT_ERR_UNSUPPORTED_SIZE;
     } else {
@@ -403,7 +413,9 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
             p->grid_cap = persistent_grid(*p->rv);
             if (p->grid_cap <= 0) st = GBFFT_ERR_CUDA;
         }
-        if (st == GBFFT_OK) st = alloc_stage_tables(&p->tw, n, p->rv->radix, p->rv->nstages);
+        if (st == GBFFT_OK)
+            st = p->rv->kind == kRowsCluster ? alloc_cluster_tables(&p->tw, *p->rv)
+                                             : alloc_stage_tables(&p->tw, n, p->rv->radix, p->rv->nstages);
     }
     // Tables are built on the legacy stream and complete before the plan is returned.
     if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
@@ -590,7 +602,7 @@ gbfft_status gbfft_plan_create_formula(gbfft_plan* out, const char* formula, int
     int exact = -1, multi = -1;
     if (dtype == GBFFT_C2C_F32 || dtype == GBFFT_C2C_F64) {
         const RowsVariant* cands[kMaxVariantsPerSize];
-        const int nc = dtype == GBFFT_C2C_F32 ? rows_variants_for(n, cands, kMaxVariantsPerSize)
+        const int nc = dtype == GBFFT_C2C_F32 ? onepass_variants_for(n, cands, kMaxVariantsPerSize)
                                               : rows_variants_f64_for(n, cands, kMaxVariantsPerSize);
         std::vector<int64_t> want = leaves;
         std::sort(want.begin(), want.end());
@@ -822,12 +834,12 @@ int gbfft_ragged_tile_split(gbfft_plan p, int64_t n) {
     return ragged_class_split(p->ragged, n);
 }
 
-int gbfft_num_variants(int64_t n) { return rows_variants_for(n, nullptr, 0); }
+int gbfft_num_variants(int64_t n) { return onepass_variants_for(n, nullptr, 0); }
 
 gbfft_status gbfft_variant_info(int64_t n, int index, int* nstages, int* radices, int* rows_per_cta,
                                 int* threads_per_cta, int* smem_bytes) {
     const RowsVariant* cands[kMaxVariantsPerSize];
-    const int nc = rows_variants_for(n, cands, kMaxVariantsPerSize);
+    const int nc = onepass_variants_for(n, cands, kMaxVariantsPerSize);
     if (index < 0 || index >= nc) return GBFFT_ERR_NOT_FOUND;
     const RowsVariant* v = cands[index];
     if (nstages) *nstages = v->nstages;
@@ -843,7 +855,7 @@ int gbfft_plan_grid_cap(gbfft_plan p) { return p ? p->grid_cap : -1; }
 
 int gbfft_variant_kind(int64_t n, int index) {
     const RowsVariant* cands[kMaxVariantsPerSize];
-    const int nc = rows_variants_for(n, cands, kMaxVariantsPerSize);
+    const int nc = onepass_variants_for(n, cands, kMaxVariantsPerSize);
     if (index < 0 || index >= nc) return -1;
     return cands[index]->kind;
 }

@@ -1,0 +1,183 @@
+// One-pass transforms for 4096 < N <= 32768 on thread-block clusters.
+//
+// Eq. 2 with N = K * M, DFT_N = (DFT_K (x) I_M) D^N_M (I_K (x) DFT_M) Pi^N_K,
+// run by a cluster of K CTAs (K = 2, 4, 8) on one row, the row staying on chip
+// between the factors: CTA k owns column k of the K x M view.
+//   A. CTA k reads the contiguous block [k*M, (k+1)*M) of the row from HBM and
+//      sends element i to column i mod K, slot i div K (Pi^N_K) in the
+//      distributed shared memory of the cluster.
+//   B. Each CTA transforms its column with the single-pass Stockham engine
+//      (I_K (x) DFT_M: the column's schedule, exchanges in its own shared
+//      memory) and multiplies by its slice of D^N_M, w_N^(j1*k).
+//   C. CTA c takes outputs j1 in [c*M/K, (c+1)*M/K): it reads z_k[j1] from all
+//      K columns, applies DFT_K (DFT_K (x) I_M) and writes y[j2*M + j1] to HBM,
+//      consecutive threads on consecutive j1.
+// One HBM round trip instead of the two of the two-pass form; the exchanges
+// between the factors go through distributed shared memory.  The cluster
+// barriers are hardware barriers of the co-scheduled cluster (no spin on
+// memory), every CTA of a cluster runs the same sequence of them, the first
+// precedes any access to another CTA's shared memory (which is valid only once
+// that CTA runs) and the last follows every such access (so that no CTA exits
+// while its shared memory is still read).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "stockham.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace gbfft {
+namespace {
+
+// The column's I/O for the Stockham engine: it reads the column from shared
+// memory and writes it back multiplied by the column's slice of D^N_M.
+template <int S>
+struct ColumnIO {
+    const float2* in;
+    float2* out;
+    const float2* __restrict__ post;  // w_N^(j1*k), j1 < M, of this CTA's column k
+    __device__ __forceinline__ float2 ld(int, int n) const { return in[n]; }
+    __device__ __forceinline__ void st(int, int n, float2 v) const { out[n] = twiddle<S>(v, __ldg(post + n)); }
+};
+
+template <int N, int K, int S, int TPB, int PS, int... Rs>
+__global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB)
+    k_stockham_cluster(const float2* in, float2* out, const float2* __restrict__ tw, long long batch) {
+    constexpr int M = N / K;
+    constexpr int E = capacity_of_r<M, 1, TPB, Rs...>();
+    constexpr int STW = StageTwiddles<1, Rs...>::value;  // the column schedule's stage blocks; D^N_M follows
+    static_assert((Rs * ...) == M, "column schedule must multiply to N / K");
+    static_assert(M % TPB == 0 && M % K == 0, "column and output slices must split evenly");
+    extern __shared__ float2 csm[];
+    float2* const col = csm;       // column k (natural order), later z_k
+    float2* const xbuf = csm + M;  // the column stages' exchange buffer (padded)
+    cg::cluster_group cluster = cg::this_cluster();
+    const int k = (int)cluster.block_rank();
+    const long long row = blockIdx.x / K;  // one row per cluster; the grid holds exactly batch clusters
+    const int tid = threadIdx.x;
+    (void)batch;
+
+    // A. block k of the row -> columns (Pi^N_K); all loads are issued before the remote stores.
+    // Another CTA's shared memory may be written only once that CTA is running: the cluster
+    // barrier below is passed only when every CTA of the cluster has started.  (Staging the block
+    // locally to send 16-byte pieces measured slower than these 8-byte stores.)
+    const float2* x = in + row * N + (long long)k * M;
+    {
+        constexpr int NE = M / TPB;
+        float2 a[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) a[e] = x[tid + e * TPB];
+        cluster.sync();
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const int i = k * M + tid + e * TPB;
+            float2* dst = cluster.map_shared_rank(col, i % K);
+            dst[i / K] = a[e];
+        }
+    }
+    cluster.sync();
+
+    // B. I_K (x) DFT_M on this column, then D^N_M
+    const ColumnIO<S> io{col, col, tw + STW + (long long)k * M};
+    float2 v[E];
+    gather_global<M, E, 1, First<Rs...>::value, ColumnIO<S>, TPB>(v, io, 1);
+    run_stages_t<M, S, E, 1, PS, TPB, false, 0, 1, Rs...>(v, io, xbuf, tw, 1);
+    cluster.sync();
+
+    // C. DFT_K (x) I_M across the columns, straight to HBM
+    constexpr int J = M / K;
+    float2* y = out + row * N;
+    const float2* cols[K];
+#pragma unroll
+    for (int kk = 0; kk < K; ++kk) cols[kk] = cluster.map_shared_rank(col, kk);
+    constexpr int NJ = (J + TPB - 1) / TPB;  // outputs per thread: every remote load issued first
+    float2 a[NJ][K];
+#pragma unroll
+    for (int e = 0; e < NJ; ++e) {
+        const int jj = tid + e * TPB;
+        if (jj < J) {
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) a[e][kk] = cols[kk][k * J + jj];
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < NJ; ++e) {
+        const int jj = tid + e * TPB;
+        if (jj < J) {
+            const int j1 = k * J + jj;
+            Dft<S, K>::run(a[e]);
+#pragma unroll
+            for (int j2 = 0; j2 < K; ++j2) y[(long long)j2 * M + j1] = a[e][j2];
+        }
+    }
+    cluster.sync();  // no CTA leaves while the others still read its column
+}
+
+template <int N, int K, int TPB, int PS, int... Rs>
+RowsVariant make_cluster_variant() {
+    constexpr int M = N / K;
+    return RowsVariant{kRowsCluster,
+                       N,
+                       capacity_of_r<M, 1, TPB, Rs...>(),
+                       1,
+                       TPB,
+                       PS,
+                       (int)sizeof...(Rs) + 1,
+                       {Rs..., K},
+                       (int)((M + smem_elems<1, M, PS>()) * sizeof(float2)),
+                       (const void*)&k_stockham_cluster<N, K, -1, TPB, PS, Rs...>,
+                       (const void*)&k_stockham_cluster<N, K, +1, TPB, PS, Rs...>};
+}
+
+#define GBFFT_CLUSTER(N, K, TPB, PS, ...) make_cluster_variant<N, K, TPB, PS, __VA_ARGS__>()
+
+// Column schedules are the single-pass ones of the same lengths; the radix
+// list of a variant is the column schedule followed by K.
+const RowsVariant kCluster[] = {
+    GBFFT_CLUSTER(5120, 2, 160, 5, 5, 16, 16, 2),
+    GBFFT_CLUSTER(6144, 2, 192, 4, 3, 16, 16, 4),
+    GBFFT_CLUSTER(7168, 2, 224, 4, 7, 16, 16, 2),
+    GBFFT_CLUSTER(8192, 2, 256, 4, 16, 16, 16),
+    GBFFT_CLUSTER(8192, 4, 128, 4, 16, 16, 8),
+    GBFFT_CLUSTER(10240, 4, 160, 5, 5, 16, 16, 2),
+    GBFFT_CLUSTER(12288, 4, 192, 4, 3, 16, 16, 4),
+    GBFFT_CLUSTER(14336, 4, 224, 4, 7, 16, 16, 2),
+    GBFFT_CLUSTER(16384, 4, 256, 4, 16, 16, 16),
+    GBFFT_CLUSTER(16384, 8, 128, 4, 16, 16, 8),
+    GBFFT_CLUSTER(20480, 8, 160, 5, 5, 16, 16, 2),
+    GBFFT_CLUSTER(24576, 8, 192, 4, 3, 16, 16, 4),
+    GBFFT_CLUSTER(28672, 8, 224, 4, 7, 16, 16, 2),
+    GBFFT_CLUSTER(32768, 8, 256, 4, 16, 16, 16),
+};
+
+}  // namespace
+
+int cluster_variants_for(int64_t n, const RowsVariant** out, int max_out) {
+    int found = 0;
+    for (const RowsVariant& v : kCluster) {
+        if (v.n != n) continue;
+        if (found < max_out && out) out[found] = &v;
+        ++found;
+    }
+    return found;
+}
+
+// Stage blocks of the column schedule (length M = N / K) followed by the
+// D^N_M table in the layout post[k*M + j1] = w_N^(j1*k).
+gbfft_status alloc_cluster_tables(float2** dst, const RowsVariant& v) {
+    const int K = v.radix[v.nstages - 1];
+    const int64_t m = v.n / K;
+    const int cnt = stage_twiddle_count(v.radix, v.nstages - 1);
+    if (cudaMalloc(dst, sizeof(float2) * ((size_t)cnt + (size_t)v.n)) != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return GBFFT_ERR_OOM;
+    }
+    if (launch_stage_twiddles(*dst, m, v.radix, v.nstages - 1, 0) != cudaSuccess ||
+        launch_post_twiddles(*dst + cnt, v.n, m, 0) != cudaSuccess)
+        return GBFFT_ERR_CUDA;
+    return GBFFT_OK;
+}
+
+}  // namespace gbfft

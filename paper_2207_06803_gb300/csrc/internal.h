@@ -17,7 +17,8 @@ enum RowsKind : int {
     kRowsDirect = 0,      // k_stockham_rows: one tile per CTA
     kRowsPersistent = 1,  // k_stockham_rows_pf: resident CTAs walk tiles with register prefetch
     kRowsSmall = 2,       // k_stockham_small: one row per thread, tile staged through shared memory
-    kRowsTma = 3          // k_stockham_rows_tma: persistent, next tile prefetched by TMA bulk copy
+    kRowsTma = 3,         // k_stockham_rows_tma: persistent, next tile prefetched by TMA bulk copy
+    kRowsCluster = 4      // k_stockham_cluster: one row per cluster of K CTAs (Eq. 2 on chip), N > 4096
 };
 
 // One compiled single-pass kernel (both directions) for transform length n.
@@ -143,6 +144,13 @@ int rows_variants_f64_for(int64_t n, const RowsVariant** out, int max_out);
 
 // All variants for length n, in preference order (the first is the default).
 int rows_variants_for(int64_t n, const RowsVariant** out, int max_out);
+// One-pass cluster variants for 4096 < n <= 32768 (cluster.cu); their radix
+// list is the column schedule followed by the cluster size K.
+int cluster_variants_for(int64_t n, const RowsVariant** out, int max_out);
+// The one-pass variants of a length: single-CTA rows kernels, else cluster kernels.
+int onepass_variants_for(int64_t n, const RowsVariant** out, int max_out);
+// Twiddle tables of a cluster variant: the column's stage blocks, then D^N_M.
+gbfft_status alloc_cluster_tables(float2** dst, const RowsVariant& v);
 
 // Largest useful grid for a persistent variant on the current device:
 // resident CTAs per SM times the SM count (0 on error).

@@ -34,9 +34,9 @@ def check(y, x, direction):
 
 @pytest.mark.parametrize("direction", [-1, 1])
 @pytest.mark.parametrize("n", [5120, 6144, 7168, 8192, 10240, 12288, 14336, 16384])
-def test_long_family_sizes_default_plan(n, direction):
+def test_long_family_sizes_two_pass_plan(n, direction):
     x = synth.uniform_batch(SEED + n, n, 3)
-    y, info = run(x, direction)
+    y, info = run(x, direction, k_outer=0)  # the two-pass form with the planner's split
     assert info["k_outer"] * info["m_inner"] == n and info["k_outer"] > 1
     assert info["workspace_bytes"] == 8 * n * 3
     check(y, x, direction)
