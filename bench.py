@@ -464,7 +464,8 @@ def other_configs(args):
             out[name] = {k: res[k] for k in ("ragged_graph_tuned_us", "ragged_gbs", "per_size_us", "per_transform_us",
                                              "speedup_vs_per_size", "speedup_vs_per_transform", "items")}
         else:
-            out[name] = {"batching": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s", "gb_per_s")}
+            out[name] = {"batching": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s", "gb_per_s",
+                                                               "service_over_10ms")}
                                       for rate, v in r["batching"].items()},
                          "serial_queue": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s")}
                                           for rate, v in r["serial_queue"].items()}}
@@ -795,8 +796,16 @@ def run_serving(args, rates=(1000, 2000, 5000, 10000, 20000, 50000), scale=1.0, 
         for t in tickets:
             srv.wait(t, 300.0)
         st = srv.stats()
+        tm = np.array([srv.timing(t) for t in tickets])
         for t in tickets:
             srv.release(t)
+        q, lat = tm[:, 0], tm[:, 1]
+        service = lat - q
+        st.update({"p999_s": float(np.percentile(lat, 99.9)), "queue_p99_s": float(np.percentile(q, 99)),
+                   # requests whose device-side service (copies in, transform, copies out) took over 10 ms:
+                   # a non-zero count marks a pause of the device or driver during the run
+                   "service_over_10ms": int((service > 0.01).sum()),
+                   "max_service_s": float(service.max())})
         return st
 
     with gbfft.Server(mem_budget_bytes=budget, n_streams=4) as srv:

@@ -374,7 +374,10 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
  * A host callback after each group's copies back stamps completion; latency
  * is completion - arrival.
  * gbfft_server_poll: *done = 1 finished, 0 pending, -1 failed/cancelled;
- * *latency_s once finished.  gbfft_server_wait blocks up to timeout_s
+ * *latency_s once finished.  gbfft_server_timing splits a finished request's
+ * latency: *queued_s = admission - arrival (waiting in the server's queue),
+ * *latency_s as gbfft_server_poll (INVALID_ARG until finished).
+ * gbfft_server_wait blocks up to timeout_s
  * (TIMEOUT otherwise).  gbfft_server_release forgets a finished ticket.
  * gbfft_server_replay submits `count` requests at arrival offsets arrival_s[i]
  * (seconds after the call, non-decreasing) from the calling thread - an open
@@ -394,6 +397,7 @@ gbfft_status gbfft_server_prepare(gbfft_server srv, int64_t n, int direction);
 gbfft_status gbfft_server_submit(gbfft_server srv, int64_t n, int64_t batch, int direction, const void *host_in,
                                  void *host_out, uint64_t *ticket);
 gbfft_status gbfft_server_poll(gbfft_server srv, uint64_t ticket, int *done, double *latency_s);
+gbfft_status gbfft_server_timing(gbfft_server srv, uint64_t ticket, double *queued_s, double *latency_s);
 gbfft_status gbfft_server_wait(gbfft_server srv, uint64_t ticket, double timeout_s);
 gbfft_status gbfft_server_release(gbfft_server srv, uint64_t ticket);
 gbfft_status gbfft_server_replay(gbfft_server srv, int64_t count, const int64_t *n, const int64_t *batch,

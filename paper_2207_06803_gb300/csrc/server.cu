@@ -109,8 +109,9 @@ struct Request {
     int direction;
     const void* in;
     void* out;
-    Clock::time_point arrival;
+    Clock::time_point arrival, admitted;
     double latency = 0;
+    double queued = 0;  // admitted - arrival: waiting in the server queue
     int state = kQueued;
 };
 
@@ -124,8 +125,11 @@ struct Group {
 
 }  // namespace
 
+constexpr size_t kWarmScratchBytes = size_t(4) << 20;  // one row (and its two-pass workspace) up to N = 262144
+
 struct Server {
     int device = 0;
+    float2* scratch = nullptr;  // kWarmScratchBytes, for the warm-up launch of each new plan
     size_t budget = 0;
     bool serial = false;
     char* arena_base = nullptr;
@@ -180,7 +184,7 @@ gbfft_status get_plan(Server* s, int64_t n, int dir, ServerPlan** out) {
     } else {
         static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
         for (int64_t m : pref)
-            if (n % m == 0 && cols_variant_for(m) && cols_variant_for(n / m)) {
+            if (n % m == 0 && (n / m) % 16 == 0 && cols_variant_for(m) && cols_variant_for(n / m)) {
                 sp.m = m;
                 sp.k = n / m;
                 break;
@@ -200,6 +204,20 @@ gbfft_status get_plan(Server* s, int64_t n, int dir, ServerPlan** out) {
             launch_stage_twiddles(sp.tw_k, sp.k, sp.ck->radix, sp.ck->nstages, s->tstream) != cudaSuccess ||
             launch_post_twiddles(sp.post, n, sp.m, s->tstream) != cudaSuccess)
             return GBFFT_ERR_CUDA;
+    }
+    // Run the plan once on one row of the server's own scratch buffer: the first launch of a kernel
+    // loads its module, which must not happen inside a request's latency.
+    if ((size_t)n * 2 * sizeof(float2) <= kWarmScratchBytes) {
+        float2* scratch = s->scratch;
+        if (!sp.two_pass) {
+            if (launch_rows(*sp.rv, dir, scratch, scratch, sp.tw, 1, sp.grid_cap, s->tstream, s->status) != cudaSuccess)
+                return GBFFT_ERR_CUDA;
+        } else {
+            float2* ws = scratch + n;
+            if (launch_cols(*sp.cm, 1, dir, scratch, ws, sp.tw_m, sp.post, 1, (int)sp.k, s->tstream) != cudaSuccess ||
+                launch_cols(*sp.ck, 2, dir, ws, scratch, sp.tw_k, nullptr, 1, (int)sp.m, s->tstream) != cudaSuccess)
+                return GBFFT_ERR_CUDA;
+        }
     }
     if (cudaStreamSynchronize(s->tstream) != cudaSuccess) return GBFFT_ERR_CUDA;
     auto res = s->plans.emplace(key, sp);
@@ -256,6 +274,7 @@ void worker_main(Server* s) {
             if (g->done.load(std::memory_order_acquire)) {
                 for (Request* r : g->reqs) {
                     r->latency = seconds_since(r->arrival, g->completed);
+                    r->queued = seconds_since(r->arrival, r->admitted);
                     r->state = kDone;
                     s->latencies.push_back(r->latency);
                     s->bytes_done += 16.0 * (double)r->n * (double)r->batch;
@@ -298,7 +317,11 @@ void worker_main(Server* s) {
             if (!s->arena->alloc(g->bytes, &g->off)) return false;
             g->stream = s->streams[(size_t)s->next_stream];
             s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
-            for (Request* r : g->reqs) r->state = kRunning;
+            const Clock::time_point now = Clock::now();
+            for (Request* r : g->reqs) {
+                r->state = kRunning;
+                r->admitted = now;
+            }
             if (!launch_group(s, g.get(), sp, n, dir, rows)) {
                 s->error = GBFFT_ERR_CUDA;
                 for (Request* r : g->reqs) r->state = kFailed;
@@ -370,7 +393,8 @@ gbfft_status server_create(Server** out, size_t budget, int n_streams, int flags
         return GBFFT_ERR_OOM;
     }
     s->arena.reset(new Arena(budget));
-    if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess || cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&s->status, sizeof(int)) != cudaSuccess || cudaMemset(s->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&s->scratch, kWarmScratchBytes) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(s->arena_base);
         delete s;
@@ -404,7 +428,7 @@ gbfft_status server_submit(Server* s, int64_t n, int64_t batch, int direction, c
         bool ok = false;
         static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
         for (int64_t m : pref)
-            if (n % m == 0 && cols_variant_for(m) && cols_variant_for(n / m)) ok = true;
+            if (n % m == 0 && (n / m) % 16 == 0 && cols_variant_for(m) && cols_variant_for(n / m)) ok = true;
         if (!ok) return GBFFT_ERR_UNSUPPORTED_SIZE;
     }
     if (slot_bytes(n, batch, needs_two_pass(n)) + 256 > s->budget) return GBFFT_ERR_BUDGET;
@@ -440,6 +464,17 @@ gbfft_status server_poll(Server* s, uint64_t ticket, int* done, double* latency)
     if (done) *done = r->state == kDone ? 1 : (r->state == kFailed || r->state == kCancelled ? -1 : 0);
     if (latency) *latency = r->latency;
     return r->state == kFailed ? (s->error ? (gbfft_status)s->error : GBFFT_ERR_CUDA) : GBFFT_OK;
+}
+
+gbfft_status server_timing(Server* s, uint64_t ticket, double* queued, double* latency) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->table.find(ticket);
+    if (it == s->table.end()) return GBFFT_ERR_NOT_FOUND;
+    const Request* r = it->second.get();
+    if (r->state != kDone) return GBFFT_ERR_INVALID_ARG;
+    if (queued) *queued = r->queued;
+    if (latency) *latency = r->latency;
+    return GBFFT_OK;
 }
 
 gbfft_status server_wait(Server* s, uint64_t ticket, double timeout_s) {
@@ -539,6 +574,7 @@ void server_destroy(Server* s) {
     }
     cudaFree(s->arena_base);
     cudaFree(s->status);
+    if (s->scratch) cudaFree(s->scratch);
     delete s;
 }
 
@@ -570,6 +606,11 @@ gbfft_status gbfft_server_prepare(gbfft_server srv, int64_t n, int direction) {
 gbfft_status gbfft_server_poll(gbfft_server srv, uint64_t ticket, int* done, double* latency_s) {
     if (!srv) return GBFFT_ERR_INVALID_ARG;
     return server_poll(reinterpret_cast<Server*>(srv), ticket, done, latency_s);
+}
+
+gbfft_status gbfft_server_timing(gbfft_server srv, uint64_t ticket, double* queued_s, double* latency_s) {
+    if (!srv) return GBFFT_ERR_INVALID_ARG;
+    return server_timing(reinterpret_cast<Server*>(srv), ticket, queued_s, latency_s);
 }
 
 gbfft_status gbfft_server_wait(gbfft_server srv, uint64_t ticket, double timeout_s) {

@@ -82,6 +82,8 @@ PROTOTYPES = {
     "gbfft_ragged_schedule": (_c_int, [_c_vp, _c_i64, _c_intp]),
     "gbfft_plan_create_nd": (_c_int, [ctypes.POINTER(_c_vp), _c_int, _c_i64p, _c_i64, _c_int, _c_int]),
     "gbfft_plan_dims": (_c_int, [_c_vp, _c_intp, _c_i64p]),
+    "gbfft_server_timing": (_c_int, [_c_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "gbfft_formula_check": (_c_int, [ctypes.c_char_p, _c_i64p, _c_intp, _c_int, _c_intp, _c_i64p, ctypes.c_char_p,
                                      ctypes.c_size_t]),
     "gbfft_plan_create_formula": (_c_int, [ctypes.POINTER(_c_vp), ctypes.c_char_p, _c_i64, _c_int, _c_int, _c_intp]),
@@ -427,6 +429,13 @@ def gbfft_server_poll(srv: int, ticket: int) -> tuple[int, float]:
     return done.value, lat.value
 
 
+def gbfft_server_timing(srv: int, ticket: int) -> tuple[float, float]:
+    """(seconds queued before admission, total latency) of a finished request."""
+    q, lat = ctypes.c_double(), ctypes.c_double()
+    _check(lib().gbfft_server_timing(srv, ticket, ctypes.byref(q), ctypes.byref(lat)), "gbfft_server_timing")
+    return q.value, lat.value
+
+
 def gbfft_server_wait(srv: int, ticket: int, timeout_s: float = 60.0) -> None:
     _check(lib().gbfft_server_wait(srv, ticket, timeout_s), "gbfft_server_wait")
 
@@ -476,6 +485,9 @@ class Server:
 
     def poll(self, ticket: int) -> tuple[int, float]:
         return gbfft_server_poll(self.handle, ticket)
+
+    def timing(self, ticket: int) -> tuple[float, float]:
+        return gbfft_server_timing(self.handle, ticket)
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
         gbfft_server_wait(self.handle, ticket, timeout_s)

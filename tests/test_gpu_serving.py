@@ -40,6 +40,8 @@ def test_mix_equals_alone_and_oracle():
             srv.wait(t, 60.0)
             done, lat = srv.poll(t)
             assert done == 1 and lat > 0
+            queued, lat2 = srv.timing(t)
+            assert lat2 == lat and 0 <= queued <= lat
         st = srv.stats()
         assert st["completed"] == len(ns)
         assert 0 < st["p50_s"] <= st["p99_s"] <= st["max_s"]
