@@ -371,8 +371,8 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
  * pool: requests arriving while earlier groups run are admitted as memory
  * frees up and overlap them.  Schedules and twiddle tables are built once per
  * (n, direction) and stay resident (gbfft_server_prepare builds them ahead).
- * A host callback after each group's copies back stamps completion; latency
- * is completion - arrival.
+ * An event recorded after each group's copies back, polled by the worker,
+ * stamps completion; latency is completion - arrival.
  * gbfft_server_poll: *done = 1 finished, 0 pending, -1 failed/cancelled;
  * *latency_s once finished.  gbfft_server_timing splits a finished request's
  * latency: *queued_s = admission - arrival (waiting in the server's queue),

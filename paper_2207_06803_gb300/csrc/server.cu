@@ -16,15 +16,17 @@
 //               earlier groups' work.
 //   plans       per (n, direction) the schedule and its twiddle tables are
 //               built once and stay resident.
-//   completion  a host function enqueued after a group's device-to-host
-//               copies stamps the completion time; the worker then frees the
-//               slot.  Latency = completion - arrival.
+//   completion  an event recorded after a group's device-to-host copies;
+//               the worker polls it, stamps the completion time when it
+//               finds it complete and frees the slot.  Latency = completion -
+//               arrival.  (Host-function callbacks were used first; runs of
+//               a few seconds then showed pauses of 40-120 ms in the device-
+//               side service of a few hundred requests.)
 // Serial mode (one stream, one request per group, one request in flight) is
 // the naive queue the batching loop is compared with.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
@@ -119,7 +121,7 @@ struct Group {
     std::vector<Request*> reqs;
     size_t off = 0, bytes = 0;
     cudaStream_t stream = nullptr;
-    std::atomic<int> done{0};
+    cudaEvent_t ev = nullptr;  // recorded after the group's copies back
     Clock::time_point completed;
 };
 
@@ -145,6 +147,7 @@ struct Server {
     std::deque<Request*> queue;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> table;
     std::vector<std::unique_ptr<Group>> inflight;
+    std::vector<cudaEvent_t> free_events, all_events;  // completion events, reused
     uint64_t next_ticket = 1;
     bool stop = false;
     std::thread worker;
@@ -158,12 +161,6 @@ struct Server {
 };
 
 namespace {
-
-void CUDART_CB on_group_done(void* p) {
-    Group* g = (Group*)p;
-    g->completed = Clock::now();
-    g->done.store(1, std::memory_order_release);
-}
 
 gbfft_status get_plan(Server* s, int64_t n, int dir, ServerPlan** out) {
     auto key = std::make_pair(n, dir);
@@ -260,7 +257,7 @@ bool launch_group(Server* s, Group* g, ServerPlan* sp, int64_t n, int dir, int64
                                    g->stream) == cudaSuccess;
         at += row_bytes * (size_t)r->batch;
     }
-    ok = ok && cudaLaunchHostFunc(g->stream, on_group_done, g) == cudaSuccess;
+    ok = ok && cudaEventRecord(g->ev, g->stream) == cudaSuccess;
     return ok;
 }
 
@@ -268,10 +265,23 @@ void worker_main(Server* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        // 1. retire finished groups
-        for (size_t i = 0; i < s->inflight.size();) {
-            Group* g = s->inflight[i].get();
-            if (g->done.load(std::memory_order_acquire)) {
+        // 1. retire finished groups.  A stream runs its groups in launch order, so only the oldest
+        //    unfinished group of each stream is queried: at most one pending query per stream,
+        //    however many groups are in flight.
+        {
+            std::vector<cudaStream_t> pending;
+            size_t keep = 0;
+            for (size_t i = 0; i < s->inflight.size(); ++i) {
+                Group* g = s->inflight[i].get();
+                const bool blocked = std::find(pending.begin(), pending.end(), g->stream) != pending.end();
+                if (blocked || cudaEventQuery(g->ev) != cudaSuccess) {
+                    if (!blocked) pending.push_back(g->stream);
+                    if (keep != i) s->inflight[keep] = std::move(s->inflight[i]);
+                    ++keep;
+                    continue;
+                }
+                g->completed = Clock::now();
+                s->free_events.push_back(g->ev);
                 for (Request* r : g->reqs) {
                     r->latency = seconds_since(r->arrival, g->completed);
                     r->queued = seconds_since(r->arrival, r->admitted);
@@ -281,11 +291,10 @@ void worker_main(Server* s) {
                 }
                 s->win_last = g->completed;
                 s->arena->release(g->off, g->bytes);
-                s->inflight.erase(s->inflight.begin() + (long)i);
+                s->inflight[i].reset();
                 s->cv.notify_all();
-            } else {
-                ++i;
             }
+            s->inflight.resize(keep);
         }
         if (s->stop && s->queue.empty() && s->inflight.empty()) break;
         // 2. admit from the head of the queue while slots fit
@@ -315,6 +324,17 @@ void worker_main(Server* s) {
             g->reqs = std::move(reqs);
             g->bytes = slot_bytes(n, rows, sp->two_pass);
             if (!s->arena->alloc(g->bytes, &g->off)) return false;
+            if (s->free_events.empty()) {
+                cudaEvent_t ev;
+                if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                    s->arena->release(g->off, g->bytes);
+                    return false;
+                }
+                s->all_events.push_back(ev);
+                s->free_events.push_back(ev);
+            }
+            g->ev = s->free_events.back();
+            s->free_events.pop_back();
             g->stream = s->streams[(size_t)s->next_stream];
             s->next_stream = (s->next_stream + 1) % (int)s->streams.size();
             const Clock::time_point now = Clock::now();
@@ -326,6 +346,7 @@ void worker_main(Server* s) {
                 s->error = GBFFT_ERR_CUDA;
                 for (Request* r : g->reqs) r->state = kFailed;
                 cudaStreamSynchronize(g->stream);
+                s->free_events.push_back(g->ev);
                 s->arena->release(g->off, g->bytes);
                 s->cv.notify_all();
                 return true;
@@ -357,12 +378,14 @@ void worker_main(Server* s) {
         for (auto& g : s->inflight) inflight_reqs += g->reqs.size();
         s->max_inflight_reqs = std::max(s->max_inflight_reqs, inflight_reqs);
         s->max_used = std::max(s->max_used, s->arena->used());
-        // 4. sleep until something changes (short timeout while work is in flight)
+        // 4. idle: sleep on the condition variable; with groups in flight, yield and poll again.
+        //    (A loop that polled the events without the lock and woke on every submission launched
+        //    one small group per arrival and measured a worse tail.)
         if (s->inflight.empty() && s->queue.empty() && !s->stop) {
             s->cv.wait_for(lk, std::chrono::milliseconds(5));
         } else {
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(s->inflight.empty() ? 0 : 10));
+            std::this_thread::yield();  // completions are observed by polling their events
             lk.lock();
         }
     }
@@ -572,6 +595,7 @@ void server_destroy(Server* s) {
         for (float2* b : bufs)
             if (b) cudaFree(b);
     }
+    for (cudaEvent_t ev : s->all_events) cudaEventDestroy(ev);
     cudaFree(s->arena_base);
     cudaFree(s->status);
     if (s->scratch) cudaFree(s->scratch);
