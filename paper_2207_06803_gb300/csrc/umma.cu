@@ -4,6 +4,10 @@
 // [yr; yi] = M [xr; xi], M = [[Fr, -Fi], [Fi, Fr]], with operands split into
 // high and low half-precision parts, Mh Xh + Mh Xl + Ml Xh, FP32 accumulation),
 // arranged for tcgen05.mma instead of warp-level mma.sync:
+//   - each CTA's next tile of rows is copied HBM -> shared memory by a bulk
+//     copy (cp.async.bulk, completing on an mbarrier) issued as soon as the
+//     first stage has read the current tile, so the load overlaps the
+//     remaining stages;
 //   - one thread per butterfly (column of 16 complex), exactly as the FP32
 //     Stockham engine: it loads its column, applies the FP32 stage twiddles,
 //     scales by an exact power of two (FP16), splits into hi/lo and writes
@@ -17,6 +21,10 @@
 //   - each warp reads back its own 32 TMEM lanes (its own 32 butterflies) with
 //     tcgen05.ld, then writes the 16 outputs with the Stockham pattern
 //     (shared-memory exchange or HBM).
+// The A operands share their shared memory with the exchange buffer of the
+// stages: a stage reads its columns from the exchange buffer, all threads
+// meet at a barrier, and only then are the operands written over it; the
+// outputs go back into it once the MMA has completed.
 // Operand layout: K-major, no swizzle; a core matrix is 8 rows x 16 bytes
 // (8 halves of K), core matrices adjacent in K are 128 bytes apart (leading
 // byte offset) and 8-row groups 512 bytes apart (stride byte offset).
@@ -58,18 +66,28 @@ __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void umma_commit(uint64_t* bar) { tc_commit(bar); }
 
 struct UmmaShared {
-    uint8_t* a_hi;       // MT tiles of 128 x 32
+    float2* stage;       // the tile's input rows, natural order (bulk copy target)
+    uint8_t* a_hi;       // MT tiles of 128 x 32, over the exchange buffer
     uint8_t* a_lo;
     uint8_t* b;          // [Mh; Ml] as 64 rows x 32 (K-major)
     float2* xbuf;        // padded exchange buffer
     uint64_t* bar;       // MMA completion
+    uint64_t* ldbar;     // bulk copy of the next tile
     uint32_t* tmem_slot; // TMEM base address written by tcgen05.alloc
+};
+
+// The next tile's bulk copy, issued by thread 0 once the first stage has read the
+// staging buffer (src == nullptr: no next tile).
+struct NextTile {
+    const float2* src;
+    uint32_t bytes;
 };
 
 // One radix-16 stage: threads own butterflies B = tid (MT*128 of them).
 template <int N, int S, int PREC, int T, int PS, int L, bool FIRST, bool LAST>
 __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShared& sh, uint32_t tmem,
-                                           const float2* __restrict__ tw, int nvalid, uint32_t& phase) {
+                                           const float2* __restrict__ tw, int nvalid, uint32_t& phase,
+                                           const NextTile& next) {
     constexpr int R = 16, NR = N / R;
     const int tid = threadIdx.x;
     const int B = tid;
@@ -79,7 +97,7 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
     for (int q = 0; q < 16; ++q) {
         const int n = j + q * NR;
         if constexpr (FIRST) {
-            x[q] = (t < nvalid) ? io.ld(t, n) : make_float2(0.f, 0.f);
+            x[q] = (t < nvalid) ? sh.stage[t * N + n] : make_float2(0.f, 0.f);
         } else {
             x[q] = sh.xbuf[spad<PS>(t * N + n)];
         }
@@ -103,6 +121,8 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
 #pragma unroll
         for (int q = 0; q < 16; ++q) x[q] = make_float2(x[q].x * sc, x[q].y * sc);
     }
+    // The operands overwrite the exchange buffer: every thread has read its column first.
+    if constexpr (!FIRST) __syncthreads();
     // Row B of Ah / Al: K index 0..15 = real parts (q), 16..31 = imaginary parts.
     {
         const int mt = B >> 7, row = B & 127;
@@ -130,6 +150,14 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
     tc_fence_after();
     constexpr int MT = T * N / 16 / 128;
     if (tid == 0) {
+        if constexpr (FIRST) {
+            // every thread has read the staging buffer: bring in the next tile behind the stages
+            if (next.src) {
+                fence_proxy_async_smem();
+                mbar_expect_tx(sh.ldbar, next.bytes);
+                tma_load_1d(sh.stage, next.src, next.bytes, sh.ldbar);
+            }
+        }
         const uint32_t idesc = instr_desc(PREC, 128, 32);
         const uint32_t b_mh = smem_u32(sh.b), b_ml = b_mh + 4 * kSbo;  // rows 0-31 = Mh, 32-63 = Ml
 #pragma unroll
@@ -162,7 +190,8 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
 #pragma unroll
     for (int m = 0; m < 16; ++m) y[m] = make_float2(d0[m] * inv_sc, d0[16 + m] * inv_sc);
     tc_fence_before();
-    if constexpr (!FIRST && !LAST) __syncthreads();  // every column of this stage has been read from xbuf
+    // the MMA has completed (every thread passed the wait), so the operands are dead and the
+    // exchange buffer may take the outputs
     const int b = j / L;
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -178,12 +207,21 @@ __device__ __forceinline__ bool umma_stage(const ContigIO<N>& io, const UmmaShar
 
 template <int N, int S, int PREC, int T, int PS, int L>
 __device__ __forceinline__ bool umma_stages(const ContigIO<N>& io, const UmmaShared& sh, uint32_t tmem,
-                                            const float2* __restrict__ tw, int nvalid, uint32_t& phase) {
+                                            const float2* __restrict__ tw, int nvalid, uint32_t& phase,
+                                            const NextTile& next) {
     constexpr bool LAST = (L * 16 == N);
-    if (!umma_stage<N, S, PREC, T, PS, L, L == 1, LAST>(io, sh, tmem, tw + (L > 1 ? L - 16 : 0), nvalid, phase))
+    if (!umma_stage<N, S, PREC, T, PS, L, L == 1, LAST>(io, sh, tmem, tw + (L > 1 ? L - 16 : 0), nvalid, phase,
+                                                        next))
         return false;
-    if constexpr (!LAST) return umma_stages<N, S, PREC, T, PS, L * 16>(io, sh, tmem, tw, nvalid, phase);
+    if constexpr (!LAST) return umma_stages<N, S, PREC, T, PS, L * 16>(io, sh, tmem, tw, nvalid, phase, next);
     return true;
+}
+
+template <int N, int T, int PS>
+constexpr int umma_union_bytes() {
+    constexpr int a = 2 * (T * N / 16 / 128) * kTileBytes;
+    constexpr int x = smem_elems<T, N, PS>() * 8;
+    return ((a > x ? a : x) + 1023) / 1024 * 1024;
 }
 
 // bmat: 64 x 32 halves in the K-major core-matrix layout (k_umma_bmat).
@@ -196,19 +234,24 @@ __global__ void __launch_bounds__(T * N / 16) k_stockham_umma(const float2* in, 
     constexpr int MT = TPB / 128;
     constexpr uint32_t kCols = MT == 1 ? 32 : 64;
     static_assert(TPB % 128 == 0 && (MT == 1 || MT == 2), "one or two M = 128 tiles per stage");
+    constexpr int kStageBytes = T * N * 8;
+    constexpr int kUnionBytes = umma_union_bytes<N, T, PS>();
     extern __shared__ __align__(1024) uint8_t usm[];
     UmmaShared sh;
-    sh.a_hi = usm;
-    sh.a_lo = usm + MT * kTileBytes;
-    sh.b = usm + 2 * MT * kTileBytes;
-    sh.xbuf = reinterpret_cast<float2*>(usm + 2 * MT * kTileBytes + 64 * kRowBytes);
-    sh.bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sh.xbuf) + smem_elems<T, N, PS>() * 8);
-    sh.tmem_slot = reinterpret_cast<uint32_t*>(sh.bar + 1);
+    sh.stage = reinterpret_cast<float2*>(usm);
+    sh.a_hi = usm + kStageBytes;
+    sh.a_lo = sh.a_hi + MT * kTileBytes;
+    sh.xbuf = reinterpret_cast<float2*>(sh.a_hi);
+    sh.b = usm + kStageBytes + kUnionBytes;
+    sh.bar = reinterpret_cast<uint64_t*>(sh.b + 64 * kRowBytes);
+    sh.ldbar = sh.bar + 1;
+    sh.tmem_slot = reinterpret_cast<uint32_t*>(sh.bar + 2);
     const int tid = threadIdx.x;
     // B operand, resident for the kernel (64 rows x 64 bytes = 256 uint4).
     for (int i = tid; i < 64 * kRowBytes / 16; i += TPB) reinterpret_cast<uint4*>(sh.b)[i] = bmat[i];
     if (tid == 0) {
         mbar_init(sh.bar, 1);
+        mbar_init(sh.ldbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (tid < 32) {
@@ -221,14 +264,27 @@ __global__ void __launch_bounds__(T * N / 16) k_stockham_umma(const float2* in, 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *sh.tmem_slot;
-    uint32_t phase = 0;
+    uint32_t phase = 0, ldphase = 0;
     const long long ntiles = (batch + T - 1) / T;
+    if (tid == 0 && blockIdx.x < ntiles) {
+        const uint32_t bytes = (uint32_t)(tile_rows(blockIdx.x, T, batch) * N * 8);
+        mbar_expect_tx(sh.ldbar, bytes);
+        tma_load_1d(sh.stage, in + (long long)blockIdx.x * T * N, bytes, sh.ldbar);
+    }
     bool ok = true;
     for (long long tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
         __syncthreads();
+        ok = __syncthreads_and(mbar_wait(sh.ldbar, ldphase, kUmmaWaitNs) ? 1 : 0);
+        if (!ok) break;  // the only copy in flight is the one that did not arrive
+        ldphase ^= 1u;
         const int nvalid = tile_rows(tile, T, batch);
-        const ContigIO<N> io{in + tile * T * N, out + tile * T * N};
-        ok = umma_stages<N, S, PREC, T, PS, 1>(io, sh, tmem, tw, nvalid, phase);
+        const long long nt = tile + gridDim.x;
+        const NextTile next{nt < ntiles ? in + nt * T * N : nullptr,
+                            nt < ntiles ? (uint32_t)(tile_rows(nt, T, batch) * N * 8) : 0u};
+        const ContigIO<N> io{nullptr, out + tile * T * N};
+        ok = umma_stages<N, S, PREC, T, PS, 1>(io, sh, tmem, tw, nvalid, phase, next);
+        // the first stage issued the next tile's copy before any wait that can fail: let it land
+        if (!ok && next.src) mbar_wait(sh.ldbar, ldphase, kUmmaWaitNs);
     }
     if (!ok && tid == 0) atomicCAS(status, 0, (int)GBFFT_ERR_TIMEOUT);
     tc_fence_before();
@@ -271,7 +327,7 @@ __global__ void k_umma_bmat(uint16_t* bm, int prec, int sign) {
 
 template <int N, int T, int PS>
 constexpr int umma_smem_bytes() {
-    return 2 * (T * N / 16 / 128) * kTileBytes + 64 * kRowBytes + smem_elems<T, N, PS>() * 8 + 16;
+    return T * N * 8 + umma_union_bytes<N, T, PS>() + 64 * kRowBytes + 32;
 }
 
 template <int N, int T, int PS>
