@@ -53,7 +53,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
-    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving", "f64", "nd"], default="sweep",
+    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving", "f64", "nd", "pease"],
+                    default="sweep",
                     help="sweep (default, the headline line) or one of the other configurations")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -586,6 +587,42 @@ def run_nd(args):
             "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_shape": rows}
 
 
+def run_pease(args):
+    """Pease's constant-geometry factorisation (variant kind 5) against the default Stockham plan on
+    the same lengths: N = 64, 256, 512, 4096 at 2^26 points per call, forward; GB/s on 16 B/point
+    and the relative L2 error of sampled rows against numpy.fft in complex128 (a spot check;
+    the parity tests compare with the oracle)."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peak, src = _peak()
+    flat = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL)
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    d_out = torch.empty_like(d_in)
+    rows = {}
+    for n in (64, 256, 512, 4096):
+        batch = TOTAL // n
+        kinds = [gbfft.gbfft_variant_kind(n, v) for v in range(gbfft.gbfft_num_variants(n))]
+        res = {}
+        for name, variant in (("stockham_default", None), ("pease", kinds.index(5))):
+            with gbfft.Plan(n, batch, -1, variant=variant) as p:
+                ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+                torch.cuda.synchronize()
+            sample = synth.sample_rows(synth.DEFAULT_SEED, batch, 16)
+            y = d_out.view(batch, 2 * n)[torch.from_numpy(sample).cuda()].cpu().numpy().view(np.complex64)
+            x = flat.reshape(batch, n)[sample].astype(np.complex128)
+            ref = np.fft.fft(x, axis=1)
+            err = float((np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)).max())
+            gbs = 16.0 * n * batch / (ms * 1e-3) / 1e9
+            res[name] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "rel_l2_max_vs_numpy_fft": err}
+        res["pease_vs_stockham"] = res["pease"]["gbs"] / res["stockham_default"]["gbs"]
+        rows[str(n)] = res
+    return {"config": "pease", "metric": "Pease constant-geometry vs Stockham c2c GB/s (16 B/point)",
+            "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_size": rows}
+
+
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64, nominal (no measured figure exists for it)
 
 
@@ -835,7 +872,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "sweep":
-        fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving,
+        fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving, "pease": run_pease,
               "f64": run_f64, "nd": run_nd}[args.config]
         print(json.dumps(fn(args)), flush=True)
         return 0

@@ -193,7 +193,10 @@ int gbfft_plan_grid_cap(gbfft_plan p);
  * Kernel shape of variant `index` for length n: 0 one tile per CTA, 1
  * persistent with register prefetch, 2 one row per thread staged through
  * shared memory, 3 persistent with the next tile prefetched by TMA bulk copy
- * into shared memory (bounded mbarrier waits).  -1 for an index out of range.
+ * into shared memory (bounded mbarrier waits), 4 one row per thread-block
+ * cluster (N > 4096, Eq. 2 on chip), 5 Pease's constant-geometry
+ * factorisation of N = R^t (stride-R reads, stride-N/R writes at every stage,
+ * digit-reversed input; one tile per CTA).  -1 for an index out of range.
  */
 int gbfft_variant_kind(int64_t n, int index);
 
@@ -264,8 +267,14 @@ gbfft_status gbfft_plan_dims(gbfft_plan p, int *rank, int64_t *dims);
  * Permute(N, K) with N = K*M, or its transpose Permute(N, M) · (I_K ⊗ DFT_M) ·
  * twiddle(N, M) · (DFT_K ⊗ I_M) (the decimation-in-frequency order: DFT_N is
  * symmetric), recursively (each DFT factor may be such a product; Eq. 1 is
- * N = 4).  On success writes N, the outermost K (0 when the
- * formula is a single DFT(N)), and the DFT leaf sizes in the order the product
+ * N = 4); or Pease's constant-geometry form for N = R^t, t >= 2 (Eq. 2 with
+ * K = R unrolled over the digits),
+ *     G_t · ... · G_1 · Rev_N,
+ *     G_s = (DFT(R) ⊗ I(N/R)) · (twiddle(R^s, R^(s-1)) ⊗ I(R^(t-s))) · Permute(N, R),
+ *     Rev_N = (I(R) ⊗ Rev_(N/R)) · Permute(N, R),  Rev_R = I(R)
+ * (G_t's twiddle factor may be written twiddle(N, N/R) alone; Rev_(R^2) may be
+ * written Permute(R^2, R)).  On success writes N, the outermost K (0 when the
+ * formula is a single DFT(N) or Pease's form), and the DFT leaf sizes in the order the product
  * applies them (rightmost first; at most `max_leaves` written, *nleaves = the
  * full count).  Host only: no CUDA call.  Errors: INVALID_ARG (syntax,
  * dimension mismatch, or not a DFT factorisation), with a message in `err`
@@ -275,12 +284,21 @@ gbfft_status gbfft_formula_check(const char *formula, int64_t *n, int *leaves, i
                                  int64_t *k_outer, char *err, size_t err_len);
 
 /*
+ * The factorisation a formula states at its top level: 0 Eq. 2 (or a single
+ * DFT(N)), 1 Eq. 2's transpose (decimation in frequency), 2 Pease's form; -1
+ * when gbfft_formula_check rejects it.  Host only.
+ */
+int gbfft_formula_form(const char *formula);
+
+/*
  * A plan for the transform a checked formula denotes, following the formula
  * as literally as the compiled kernels allow.  *match (may be NULL): 2 = the
  * formula's own factorisation (a single-pass plan whose Stockham radix
- * sequence is the formula's leaf sequence, or Eq. 2's two-pass plan with the
+ * sequence is the formula's leaf sequence, the Pease kernel for a Pease
+ * formula of a compiled length (variant kind 5), or Eq. 2's two-pass plan with the
  * formula's outermost split K x M over plain DFT(K), DFT(M) factors); 1 = the
- * same radices in another stage order, or the outermost split with the inner
+ * same radices in another stage order (a Pease formula without a compiled
+ * Pease kernel runs its radices as Stockham stages), or the outermost split with the inner
  * factors on the column kernels' own schedules; 0 = the default plan for N.
  * Errors as gbfft_formula_check (INVALID_ARG) and gbfft_plan_create.
  */

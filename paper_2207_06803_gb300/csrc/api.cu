@@ -14,11 +14,12 @@ namespace gbfft {
 
 int rows_variants_for(int64_t n, const RowsVariant** out, int max_out) {
     int found = 0;
-    const RowsVariant* tabs[2];
-    int counts[2];
+    const RowsVariant* tabs[3];
+    int counts[3];
     tabs[0] = rows_variants_pow2(&counts[0]);
     tabs[1] = rows_variants_mixed(&counts[1]);
-    for (int t = 0; t < 2; ++t) {
+    tabs[2] = rows_variants_pease(&counts[2]);  // after the Stockham variants: their indices stay put
+    for (int t = 0; t < 3; ++t) {
         for (int i = 0; i < counts[t]; ++i) {
             if (tabs[t][i].n == n) {
                 if (found < max_out && out) out[found] = &tabs[t][i];
@@ -597,8 +598,8 @@ gbfft_status gbfft_plan_create_formula(gbfft_plan* out, const char* formula, int
     if (!out) return GBFFT_ERR_INVALID_ARG;
     int64_t n = 0, k_top = 0;
     std::vector<int64_t> leaves;
-    bool bare = false;
-    if (!formula_plan_choice(formula, &n, &leaves, &k_top, &bare)) return GBFFT_ERR_INVALID_ARG;
+    bool bare = false, pease = false;
+    if (!formula_plan_choice(formula, &n, &leaves, &k_top, &bare, &pease)) return GBFFT_ERR_INVALID_ARG;
     int exact = -1, multi = -1;
     if (dtype == GBFFT_C2C_F32 || dtype == GBFFT_C2C_F64) {
         const RowsVariant* cands[kMaxVariantsPerSize];
@@ -607,10 +608,12 @@ gbfft_status gbfft_plan_create_formula(gbfft_plan* out, const char* formula, int
         std::vector<int64_t> want = leaves;
         std::sort(want.begin(), want.end());
         for (int v = 0; v < nc && v < kMaxVariantsPerSize; ++v) {
+            // the same factorisation: a Pease formula runs the Pease kernel, any other the Stockham stages
+            const bool same_form = (cands[v]->kind == kRowsPease) == pease;
             std::vector<int64_t> have(cands[v]->radix, cands[v]->radix + cands[v]->nstages);
-            if (exact < 0 && have == leaves) exact = v;
+            if (exact < 0 && same_form && have == leaves) exact = v;
             std::sort(have.begin(), have.end());
-            if (multi < 0 && have == want) multi = v;
+            if (multi < 0 && cands[v]->kind != kRowsPease && have == want) multi = v;
         }
     }
     int64_t kk = 0, mm = 0;

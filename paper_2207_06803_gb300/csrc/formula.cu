@@ -4,7 +4,8 @@
 //     DFT_N = (DFT_K ⊗ I_M) · twiddle(N, M) · (I_K ⊗ DFT_M) · Permute(N, K),  N = K M,
 // applied recursively (either DFT factor may itself be such a product; Eq. 1
 // is the case N = 4), or its transpose Permute(N, M) · (I_K ⊗ DFT_M) ·
-// twiddle(N, M) · (DFT_K ⊗ I_M) (decimation in frequency).  twiddle(N, M) is the diagonal D^N_M and Permute(N, K)
+// twiddle(N, M) · (DFT_K ⊗ I_M) (decimation in frequency), or Pease's
+// constant-geometry product for N = R^t (as_pease below).  twiddle(N, M) is the diagonal D^N_M and Permute(N, K)
 // the stride permutation Pi^N_K of Eq. 2 (their argument order follows the
 // subscripts of Eq. 2).  A checked formula then selects the execution plan:
 // its DFT leaves, in the order the product applies them (rightmost first),
@@ -223,6 +224,7 @@ struct DftForm {
     int64_t k_top = 0;            // outermost split N = K * M (0: a single DFT(n) leaf)
     bool bare = false;            // the outermost split is Eq. 2's own order over DFT(K), DFT(M) leaves
     bool transposed = false;      // the outermost split is the transposed (decimation-in-frequency) form
+    bool pease = false;           // the whole formula is Pease's constant-geometry product
     std::vector<int64_t> leaves;  // DFT leaf sizes in application order
 };
 
@@ -254,8 +256,82 @@ bool as_dft_transposed(const std::vector<const Node*>& fs, DftForm* f, std::stri
     return true;
 }
 
-// Whether n denotes DFT_N: a DFT(n) leaf, or Eq. 2's four factors (or their
-// transpose) with DFT factors that themselves denote DFTs.
+bool is_kind(const Node* n, NodeKind k, int64_t a, int64_t b = -1) {
+    return n->kind == k && n->a == a && (b < 0 || n->b == b);
+}
+
+// I(size), written as one identity or as the Kronecker product of identities.
+bool is_identity(const Node* n, int64_t size) {
+    if (n->kind == kIdent) return n->a == size;
+    if (n->kind != kKron) return false;
+    std::string e;
+    const int64_t a = dim(n->l.get(), &e);
+    return a > 0 && size % a == 0 && is_identity(n->l.get(), a) && is_identity(n->r.get(), size / a);
+}
+
+// Whether the product of `fs` is the base-R digit reversal of length N,
+//     Rev_N = (I(R) ⊗ Rev_{N/R}) · Permute(N, R),  Rev_R = I(R)
+// (with Rev_{R^2} = Permute(R^2, R) accepted without its identity factor).
+bool is_reversal(const std::vector<const Node*>& fs, int64_t N, int64_t R) {
+    if (N == R) return fs.empty() || (fs.size() == 1 && is_identity(fs[0], R));
+    if (fs.size() == 1) return N == R * R && is_kind(fs[0], kPermute, N, R);
+    if (fs.size() != 2 || !is_kind(fs[1], kPermute, N, R)) return false;
+    const Node* k = fs[0];
+    if (k->kind != kKron || !is_identity(k->l.get(), R)) return false;
+    std::vector<const Node*> inner;
+    flatten_product(k->r.get(), &inner);
+    return is_reversal(inner, N / R, R);
+}
+
+// Pease's constant-geometry form of DFT_N, N = R^t, t >= 2 (Eq. 2 with K = R
+// unrolled over the digits, the permutations gathered into one digit reversal
+// applied first):
+//     DFT_N = G_t · ... · G_1 · Rev_N,
+//     G_s   = (DFT(R) ⊗ I(N/R)) · (twiddle(R^s, R^(s-1)) ⊗ I(R^(t-s))) · Permute(N, R),
+// where G_t's twiddle factor may be written twiddle(N, N/R) alone (its
+// identity is I(1)).  Its DFT leaves are t copies of DFT(R).
+bool as_pease(const std::vector<const Node*>& fs, DftForm* f, std::string* err) {
+    const Node* f0 = fs[0];
+    if (f0->kind != kKron || f0->l->kind != kDft || f0->r->kind != kIdent || f0->l->a < 2)
+        return *err = "Pease form: first factor must be (DFT(R) (x) I(N/R))", false;
+    const int64_t R = f0->l->a, N = R * f0->r->a;
+    int t = 0;
+    for (int64_t m = 1; m < N; m *= R) ++t;
+    int64_t p = 1;
+    for (int i = 0; i < t; ++i) p *= R;
+    if (p != N || t < 2) return *err = "Pease form: N must be a power of R with at least two stages", false;
+    if (fs.size() < (size_t)(3 * t)) return *err = "Pease form: three factors per stage, t stages for N = R^t", false;
+    int64_t rs = N;  // R^s for the stage s = t - i
+    for (int i = 0; i < t; ++i, rs /= R) {
+        const int s = t - i;
+        const Node *a = fs[3 * i], *b = fs[3 * i + 1], *c = fs[3 * i + 2];
+        if (a->kind != kKron || !is_kind(a->l.get(), kDft, R) || !is_identity(a->r.get(), N / R))
+            return *err = "Pease form, stage " + std::to_string(s) + ": expected (DFT(R) (x) I(N/R))", false;
+        const bool tw_ok =
+            (b->kind == kKron && is_kind(b->l.get(), kTwiddle, rs, rs / R) && is_identity(b->r.get(), N / rs)) ||
+            (rs == N && is_kind(b, kTwiddle, N, N / R));
+        if (!tw_ok)
+            return *err = "Pease form, stage " + std::to_string(s) + ": expected (twiddle(R^s, R^(s-1)) (x) I(R^(t-s)))",
+                   false;
+        if (!is_kind(c, kPermute, N, R))
+            return *err = "Pease form, stage " + std::to_string(s) + ": expected Permute(N, R)", false;
+    }
+    const std::vector<const Node*> rest(fs.begin() + 3 * t, fs.end());
+    if (!is_reversal(rest, N, R))
+        return *err = "Pease form: the stages must be followed by the digit reversal "
+                      "Rev_N = (I(R) (x) Rev_(N/R)) . Permute(N, R), Rev_R = I(R)",
+               false;
+    f->n = N;
+    f->k_top = 0;
+    f->bare = false;
+    f->transposed = false;
+    f->pease = true;
+    f->leaves.assign((size_t)t, R);
+    return true;
+}
+
+// Whether n denotes DFT_N: a DFT(n) leaf, Eq. 2's four factors (or their
+// transpose) with DFT factors that themselves denote DFTs, or Pease's form.
 bool as_dft(const Node* n, DftForm* f, std::string* err) {
     if (n->kind == kDft) {
         f->n = n->a;
@@ -267,6 +343,11 @@ bool as_dft(const Node* n, DftForm* f, std::string* err) {
     std::vector<const Node*> fs;
     flatten_product(n, &fs);
     if (fs.size() == 1) return as_dft(fs[0], f, err);
+    if (fs.size() >= 7) {
+        std::string pe;
+        if (as_pease(fs, f, &pe)) return true;
+        return *err = "not a DFT: Eq. 2 has four factors (or their transpose); " + pe, false;
+    }
     if (fs.size() != 4)
         return *err = "not a DFT: Eq. 2 has four factors (DFT_K (x) I_M) . twiddle(N,M) . (I_K (x) DFT_M) . "
                       "Permute(N,K) (or their transpose)",
@@ -331,7 +412,8 @@ void put_err(const std::string& e, char* buf, size_t len) {
 
 }  // namespace
 
-bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* leaves, int64_t* k_top, bool* bare) {
+bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* leaves, int64_t* k_top, bool* bare,
+                         bool* pease) {
     DftForm f;
     std::string err;
     if (check(text, &f, &err) != GBFFT_OK) return false;
@@ -339,6 +421,7 @@ bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* lea
     *leaves = f.leaves;
     *k_top = f.k_top;
     *bare = f.bare;
+    *pease = f.pease;
     return true;
 }
 
@@ -364,6 +447,13 @@ gbfft_status gbfft_formula_check(const char* formula, int64_t* n, int* leaves, i
     if (leaves)
         for (int i = 0; i < (int)f.leaves.size() && i < max_leaves; ++i) leaves[i] = (int)f.leaves[i];
     return GBFFT_OK;
+}
+
+int gbfft_formula_form(const char* formula) {
+    DftForm f;
+    std::string e;
+    if (check(formula, &f, &e) != GBFFT_OK) return -1;
+    return f.pease ? 2 : (f.transposed ? 1 : 0);
 }
 
 }  // extern "C"

@@ -18,7 +18,8 @@ enum RowsKind : int {
     kRowsPersistent = 1,  // k_stockham_rows_pf: resident CTAs walk tiles with register prefetch
     kRowsSmall = 2,       // k_stockham_small: one row per thread, tile staged through shared memory
     kRowsTma = 3,         // k_stockham_rows_tma: persistent, next tile prefetched by TMA bulk copy
-    kRowsCluster = 4      // k_stockham_cluster: one row per cluster of K CTAs (Eq. 2 on chip), N > 4096
+    kRowsCluster = 4,     // k_stockham_cluster: one row per cluster of K CTAs (Eq. 2 on chip), N > 4096
+    kRowsPease = 5        // k_pease_rows: Pease's constant-geometry factorisation, one tile per CTA
 };
 
 // One compiled single-pass kernel (both directions) for transform length n.
@@ -129,7 +130,8 @@ bool ragged_supported(int64_t n);
 // Factorisation-formula front end (formula.cu): whether `text` denotes DFT_n by
 // Eq. 2; its DFT leaves in application order, outermost split K (0 if none) and
 // whether that split's DFT factors are plain DFT(K), DFT(M) leaves.
-bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* leaves, int64_t* k_top, bool* bare);
+bool formula_plan_choice(const char* text, int64_t* n, std::vector<int64_t>* leaves, int64_t* k_top, bool* bare,
+                         bool* pease);
 
 // Planner wisdom (autotune.cu): the autotuned choice for (n, dtype, direction).
 void wisdom_load_env_once();
@@ -138,6 +140,7 @@ bool wisdom_lookup(int64_t n, int dtype, int direction, int* variant, int64_t* k
 // Per-translation-unit variant tables, gathered by the registry in api.cu.
 const RowsVariant* rows_variants_pow2(int* count);
 const RowsVariant* rows_variants_mixed(int* count);
+const RowsVariant* rows_variants_pease(int* count);  // Pease form, N = R^t (pease.cu)
 // Complex128 / FP64 single-pass variants (rows_f64.cu).
 const RowsVariant* rows_variants_f64(int* count);
 int rows_variants_f64_for(int64_t n, const RowsVariant** out, int max_out);

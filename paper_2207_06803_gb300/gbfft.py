@@ -87,6 +87,7 @@ PROTOTYPES = {
     "gbfft_formula_check": (_c_int, [ctypes.c_char_p, _c_i64p, _c_intp, _c_int, _c_intp, _c_i64p, ctypes.c_char_p,
                                      ctypes.c_size_t]),
     "gbfft_plan_create_formula": (_c_int, [ctypes.POINTER(_c_vp), ctypes.c_char_p, _c_i64, _c_int, _c_int, _c_intp]),
+    "gbfft_formula_form": (_c_int, [ctypes.c_char_p]),
     "gbfft_ragged_set_item_ready": (_c_int, [_c_vp, _c_i64, _c_int]),
     "gbfft_ragged_set_wait_limit": (_c_int, [_c_vp, _c_i64]),
     "gbfft_server_create": (_c_int, [ctypes.POINTER(_c_vp), _c_size, _c_int, _c_int]),
@@ -337,6 +338,11 @@ def gbfft_formula_check(formula: str) -> dict:
     if rc != 0:
         raise GbfftError(rc, "gbfft_formula_check: " + err.value.decode("utf-8", "replace"))
     return {"n": n.value, "k_outer": k.value, "leaves": list(leaves[: min(nl.value, 64)])}
+
+
+def gbfft_formula_form(formula: str) -> int:
+    """0 Eq. 2 (or one DFT), 1 its transpose (DIF), 2 Pease's form, -1 rejected."""
+    return int(lib().gbfft_formula_form(formula.encode("utf-8")))
 
 
 def gbfft_plan_create_formula(formula: str, batch: int, direction: int = GBFFT_FORWARD,

@@ -67,6 +67,31 @@ def ct(radices):
     return eq2(dft(radices[-1]), ct(radices[:-1]))
 
 
+def reversal(n, r):
+    """Base-r digit reversal of length n: Rev_n = (I_r (x) Rev_(n/r)) . Permute(n, r), Rev_r = I_r."""
+    if n == r:
+        return eye(r)
+    return prod(kron(eye(r), reversal(n // r, r)), perm(n, r))
+
+
+def pease(r, t, short=False):
+    """Pease's constant-geometry product G_t ... G_1 Rev_N for N = r^t, with
+    G_s = (DFT_r (x) I_(N/r)) . (twiddle(r^s, r^(s-1)) (x) I(r^(t-s))) . Permute(N, r);
+    `short` writes G_t's twiddle without its I(1) and Rev_(r^2) as Permute(r^2, r)."""
+    n = r ** t
+    fs = []
+    for s in range(t, 0, -1):
+        twf = tw(r ** s, r ** (s - 1))
+        if not (short and s == t):
+            twf = kron(twf, eye(r ** (t - s)))
+        fs += [kron(dft(r), eye(n // r)), twf, perm(n, r)]
+    rev = reversal(n, r)
+    if short and t == 2:
+        rev = perm(n, r)
+    fs += list(rev[1:]) if rev[0] == "prod" else [rev]
+    return prod(*fs)
+
+
 def render(f, ascii_ops=False):
     k_op = " kron " if ascii_ops else f" {KRON} "
     d_op = " * " if ascii_ops else f" {DOT} "
@@ -225,6 +250,61 @@ def test_rejections_carry_a_reason(text, why):
     assert why in str(e.value), str(e.value)
 
 
+# -- Pease's constant-geometry form ------------------------------------------
+
+PEASE_CASES = [(2, 2), (2, 3), (2, 4), (3, 2), (3, 3), (4, 2), (4, 3), (5, 2), (8, 2), (16, 2)]
+
+
+@pytest.mark.parametrize("r,t", PEASE_CASES)
+def test_pease_form_is_dft_densely(r, t):
+    """Pins the reading of Pease's factorisation (derived from Eq. 2 with K = r:
+    the permutations of the unrolled recursion gathered into one digit reversal
+    applied first, each stage G_s with the same geometry) to the DFT matrix by
+    dense evaluation, and the checker to the same formulas."""
+    for short in (False, True):
+        f = pease(r, t, short)
+        assert is_dft(f), (r, t, short)
+        got = checker_accepts(render(f))
+        assert got == {"n": r ** t, "k_outer": 0, "leaves": [r] * t}, (r, t, short, got)
+        assert gbfft.gbfft_formula_form(render(f)) == 2
+
+
+def pease_mutations(r, t):
+    """Plausible mistakes in Pease's form (t >= 3): each denotes another matrix."""
+    n = r ** t
+    good = list(pease(r, t)[1:])
+    at = lambda s: 3 * (t - s)  # index of G_s's first factor
+    s2 = at(2)
+    yield "stage 2 with stage 3's twiddle", good[:s2 + 1] + [kron(tw(r ** 3, r ** 2), eye(r ** (t - 3)))] + good[s2 + 2:]
+    yield "twiddle on the other side of its identity", good[:s2 + 1] + [kron(eye(r ** (t - 2)), tw(r ** 2, r))] + good[s2 + 2:]
+    yield "stages in reverse order", sum((good[at(s):at(s) + 3] for s in range(1, t + 1)), []) + good[3 * t:]
+    yield "digit reversal dropped", good[:3 * t]
+    yield "digit reversal applied last", good[3 * t:] + good[:3 * t]
+    yield "butterfly factor transposed", [kron(eye(n // r), dft(r))] + good[1:]
+    yield "stage permutation Permute(N, N/r)", good[:2] + [perm(n, n // r)] + good[3:]
+
+
+@pytest.mark.parametrize("r,t", [(2, 3), (3, 3), (4, 3), (2, 4)])
+def test_pease_checker_rejects_what_is_not_a_dft(r, t):
+    checked = 0
+    for why, fs in pease_mutations(r, t):
+        f = prod(*fs)
+        if not size_ok(f) or is_dft(f):
+            continue
+        assert checker_accepts(render(f)) is None, why
+        assert gbfft.gbfft_formula_form(render(f)) == -1
+        checked += 1
+    assert checked >= 6
+
+
+def test_formula_form_codes():
+    assert gbfft.gbfft_formula_form("DFT(8)") == 0
+    assert gbfft.gbfft_formula_form(render(eq2(dft(4), dft(8)))) == 0
+    assert gbfft.gbfft_formula_form(render(eq2_transposed(dft(4), dft(8)))) == 1
+    assert gbfft.gbfft_formula_form(render(pease(4, 3))) == 2
+    assert gbfft.gbfft_formula_form("I(4)") == -1
+
+
 # -- formula-driven plans on the GPU -----------------------------------------
 
 def run_formula(text, x, direction=-1):
@@ -274,3 +354,25 @@ def test_formula_plans_match_the_oracle(radices, want_match, want_k):
         assert k_outer == want_k
     ref = oracle.dft(x.astype(np.complex128), -1, nthreads=ncpu())
     assert row_rel_l2(y, ref).max() <= tol_fp32(n)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("r,t", [(8, 2), (16, 2), (8, 3), (16, 3), (2, 4)])
+def test_pease_formula_plans_match_the_oracle(r, t):
+    """A Pease formula of a compiled length runs the Pease kernel (variant kind
+    5, its radices the formula's leaves); other lengths run the same radices
+    as Stockham stages, or the default plan. Both directions against the oracle,
+    67 rows (several tiles and a ragged last tile at every length)."""
+    from helpers import ncpu, row_rel_l2, tol_fp32
+    import oracle
+    n = r ** t
+    x = synth.uniform_batch(synth.DEFAULT_SEED + n, n, 67)
+    for direction in (-1, 1):
+        y, match, info, _ = run_formula(render(pease(r, t)), x, direction)
+        if n in (64, 256, 512, 4096):
+            assert match == 2 and info["radices"] == [r] * t
+            assert gbfft.gbfft_variant_kind(n, info["variant"]) == 5
+        else:
+            assert match in (0, 1)
+        ref = oracle.dft(x.astype(np.complex128), direction, nthreads=ncpu())
+        assert row_rel_l2(y, ref).max() <= tol_fp32(n), (n, direction)

@@ -211,3 +211,32 @@ def test_autotune_records_wisdom_that_plans_use(tmp_path):
         check(gpu_fft(x, -1), x, -1)  # a wisdom-driven plan still matches the oracle
     finally:
         gbfft.gbfft_wisdom_forget()
+
+
+@pytest.mark.parametrize("direction", [-1, 1])
+def test_pease_variants_at_scale(direction):
+    """Pease's constant-geometry kernels (variant kind 5) over 2^22 points plus
+    a ragged last tile, sampled rows and the last row against the oracle; the
+    guard band past the output stays untouched."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    covered = []
+    for n in single_pass_sizes():
+        for v in range(gbfft.gbfft_num_variants(n)):
+            if gbfft.gbfft_variant_kind(n, v) != 5:
+                continue
+            rows = gbfft.gbfft_variant_info(n, v)["rows_per_cta"]
+            batch = (1 << 22) // n + rows // 2 + 1
+            x = synth.uniform_batch(SEED + 5 * n, n, batch)
+            d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+            d_out = torch.full((2 * n * batch + 64,), float("nan"), device="cuda")
+            with gbfft.Plan(n, batch, direction, variant=v) as p:
+                p.execute(d_in, d_out[: 2 * n * batch])
+                torch.cuda.synchronize()
+                assert gbfft.gbfft_plan_device_status(p.handle) == 0
+            assert torch.isnan(d_out[2 * n * batch:]).all()
+            pick = np.concatenate([synth.sample_rows(SEED, batch, 48), [batch - 1]])
+            y = d_out[: 2 * n * batch].view(batch, 2 * n)[torch.from_numpy(pick).cuda()].cpu().numpy()
+            check(y.view(np.complex64), x[pick], direction)
+            covered.append(n)
+    assert sorted(covered) == [64, 256, 512, 4096]
