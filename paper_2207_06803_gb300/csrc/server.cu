@@ -342,7 +342,13 @@ void worker_main(Server* s) {
                 r->state = kRunning;
                 r->admitted = now;
             }
-            if (!launch_group(s, g.get(), sp, n, dir, rows)) {
+            // The copies and launches run without the lock: the group's requests are Running (no other
+            // thread changes or releases them), its slot and event are the worker's, and submissions
+            // need not wait behind a group's API calls.
+            lk.unlock();
+            const bool launched = launch_group(s, g.get(), sp, n, dir, rows);
+            lk.lock();
+            if (!launched) {
                 s->error = GBFFT_ERR_CUDA;
                 for (Request* r : g->reqs) r->state = kFailed;
                 cudaStreamSynchronize(g->stream);
@@ -444,7 +450,7 @@ gbfft_status server_create(Server** out, size_t budget, int n_streams, int flags
 }
 
 gbfft_status server_submit(Server* s, int64_t n, int64_t batch, int direction, const void* in, void* out,
-                           uint64_t* ticket) {
+                           uint64_t* ticket, const Clock::time_point* arrival = nullptr) {
     if (!s || !in || !out || !ticket || batch < 1 || n < 1) return GBFFT_ERR_INVALID_ARG;
     if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
     if (rows_variants_for(n, nullptr, 0) == 0) {
@@ -461,7 +467,7 @@ gbfft_status server_submit(Server* s, int64_t n, int64_t batch, int direction, c
     r->direction = direction;
     r->in = in;
     r->out = out;
-    r->arrival = Clock::now();
+    r->arrival = arrival ? *arrival : Clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stop) return GBFFT_ERR_INVALID_ARG;
     r->ticket = s->next_ticket++;
@@ -567,7 +573,9 @@ gbfft_status server_replay(Server* s, int64_t count, const int64_t* n, const int
             const auto left = due - Clock::now();
             if (left > std::chrono::microseconds(200)) std::this_thread::sleep_for(left - std::chrono::microseconds(100));
         }
-        gbfft_status st = server_submit(s, n[i], batch[i], direction[i], in[i], out[i], &tickets[i]);
+        // latency counts from the scheduled arrival: a submission that runs late (the submitting
+        // thread delayed) still owes the request its wait
+        gbfft_status st = server_submit(s, n[i], batch[i], direction[i], in[i], out[i], &tickets[i], &due);
         if (st != GBFFT_OK) return st;
     }
     return GBFFT_OK;
