@@ -77,7 +77,11 @@ int gbfft_version(void);
  * direction `direction` (GBFFT_FORWARD / GBFFT_INVERSE) and arithmetic `dtype`.
  * The planner factorises n into a radix schedule (Eq. 2 factor types) and
  * generates the twiddle table w_N^j, j < n, in FP64 on the device, rounded to
- * float32.  batch may be 0 (execute is then a no-op).  On success *out holds a
+ * float32.  For FP32 n <= 4096 runs in one pass; above, the default is Eq. 2
+ * as two passes (two HBM round trips), except n = 8192, where the one-pass
+ * kernel on a pair of CTAs of a thread-block cluster (variant kind 4) is the
+ * default because it measured faster.  batch may be 0 (execute is then a
+ * no-op).  On success *out holds a
  * new plan that the caller releases with gbfft_destroy().  Errors:
  * INVALID_ARG, UNSUPPORTED_SIZE, OOM, CUDA.  *out is set to NULL on error.
  *

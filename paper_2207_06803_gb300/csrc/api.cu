@@ -361,11 +361,14 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     const RowsVariant* cands[kMaxVariantsPerSize];
     const int nc = onepass_variants_for(n, cands, kMaxVariantsPerSize);
     int64_t kk = 0, mm = 0;
-    // Above 4096 the default is Eq. 2 as two passes: the one-pass cluster kernels (the row kept
-    // on chip, exchanged through distributed shared memory) measured slower on GB300 and are
-    // chosen only when forced or by the autotuner, or when no split exists.
+    // Above 4096 the default is Eq. 2 as two passes, except at the lengths where the one-pass
+    // cluster kernel (the row kept on chip, exchanged through distributed shared memory) measured
+    // faster on GB300 (cluster_is_default); elsewhere the cluster kernels run when forced, when
+    // the autotuner picks them, or when no split exists.
     const bool cluster_only = nc > 0 && rows_variants_for(n, nullptr, 0) == 0;
-    const bool two_pass = k_outer > 0 || (variant < 0 && (nc == 0 || (cluster_only && choose_split(n, 0, &kk, &mm))));
+    const bool two_pass =
+        k_outer > 0 ||
+        (variant < 0 && (nc == 0 || (cluster_only && !cluster_is_default(n) && choose_split(n, 0, &kk, &mm))));
     if (two_pass) {
         if (!choose_split(n, k_outer, &kk, &mm)) return k_outer > 0 ? GBFFT_ERR_NOT_FOUND : GBFFT_ERR_UNSUPPORTED_SIZE;
     } else {

@@ -30,15 +30,31 @@ namespace cg = cooperative_groups;
 namespace gbfft {
 namespace {
 
+// A cluster barrier that orders no memory: arrive.relaxed lets a CTA pass
+// without first waiting for its outstanding global loads and stores, which
+// the release fence of cluster.sync() would.  Used where the barrier only
+// has to establish that every CTA has started, or that every CTA is done
+// reading the others' shared memory (its remote loads have returned: the
+// values were consumed before the arrive in program order).
+__device__ __forceinline__ void cluster_sync_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
+}
+
 // The column's I/O for the Stockham engine: it reads the column from shared
-// memory and writes it back multiplied by the column's slice of D^N_M.
-template <int S>
+// memory and writes it back multiplied by the column's slice of D^N_M.  The
+// column lives in the stages' own (padded) exchange buffer, so the engine
+// synchronises before the first exchange (SYNC0) and before these stores.
+template <int S, int PS>
 struct ColumnIO {
+    static constexpr bool kSyncBeforeStore = true;
     const float2* in;
     float2* out;
     const float2* __restrict__ post;  // w_N^(j1*k), j1 < M, of this CTA's column k
-    __device__ __forceinline__ float2 ld(int, int n) const { return in[n]; }
-    __device__ __forceinline__ void st(int, int n, float2 v) const { out[n] = twiddle<S>(v, __ldg(post + n)); }
+    __device__ __forceinline__ float2 ld(int, int n) const { return in[spad<PS>(n)]; }
+    __device__ __forceinline__ void st(int, int n, float2 v) const {
+        out[spad<PS>(n)] = twiddle<S>(v, __ldg(post + n));
+    }
 };
 
 template <int N, int K, int S, int TPB, int PS, int... Rs>
@@ -50,8 +66,7 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB)
     static_assert((Rs * ...) == M, "column schedule must multiply to N / K");
     static_assert(M % TPB == 0 && M % K == 0, "column and output slices must split evenly");
     extern __shared__ float2 csm[];
-    float2* const col = csm;       // column k (natural order), later z_k
-    float2* const xbuf = csm + M;  // the column stages' exchange buffer (padded)
+    float2* const col = csm;  // column k, later z_k (padded slots); also the stages' exchange buffer
     cg::cluster_group cluster = cg::this_cluster();
     const int k = (int)cluster.block_rank();
     const long long row = blockIdx.x / K;  // one row per cluster; the grid holds exactly batch clusters
@@ -68,21 +83,21 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB)
         float2 a[NE];
 #pragma unroll
         for (int e = 0; e < NE; ++e) a[e] = x[tid + e * TPB];
-        cluster.sync();
+        cluster_sync_relaxed();  // every CTA of the cluster runs: its shared memory may be written
 #pragma unroll
         for (int e = 0; e < NE; ++e) {
             const int i = k * M + tid + e * TPB;
             float2* dst = cluster.map_shared_rank(col, i % K);
-            dst[i / K] = a[e];
+            dst[spad<PS>(i / K)] = a[e];
         }
     }
     cluster.sync();
 
     // B. I_K (x) DFT_M on this column, then D^N_M
-    const ColumnIO<S> io{col, col, tw + STW + (long long)k * M};
+    const ColumnIO<S, PS> io{col, col, tw + STW + (long long)k * M};
     float2 v[E];
-    gather_global<M, E, 1, First<Rs...>::value, ColumnIO<S>, TPB>(v, io, 1);
-    run_stages_t<M, S, E, 1, PS, TPB, false, 0, 1, Rs...>(v, io, xbuf, tw, 1);
+    gather_global<M, E, 1, First<Rs...>::value, ColumnIO<S, PS>, TPB>(v, io, 1);
+    run_stages_t<M, S, E, 1, PS, TPB, true, 0, 1, Rs...>(v, io, col, tw, 1);
     cluster.sync();
 
     // C. DFT_K (x) I_M across the columns, straight to HBM
@@ -98,7 +113,7 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB)
         const int jj = tid + e * TPB;
         if (jj < J) {
 #pragma unroll
-            for (int kk = 0; kk < K; ++kk) a[e][kk] = cols[kk][k * J + jj];
+            for (int kk = 0; kk < K; ++kk) a[e][kk] = cols[kk][spad<PS>(k * J + jj)];
         }
     }
 #pragma unroll
@@ -111,7 +126,7 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB)
             for (int j2 = 0; j2 < K; ++j2) y[(long long)j2 * M + j1] = a[e][j2];
         }
     }
-    cluster.sync();  // no CTA leaves while the others still read its column
+    cluster_sync_relaxed();  // no CTA leaves while the others still read its column
 }
 
 template <int N, int K, int TPB, int PS, int... Rs>
@@ -125,7 +140,7 @@ RowsVariant make_cluster_variant() {
                        PS,
                        (int)sizeof...(Rs) + 1,
                        {Rs..., K},
-                       (int)((M + smem_elems<1, M, PS>()) * sizeof(float2)),
+                       (int)(smem_elems<1, M, PS>() * sizeof(float2)),
                        (const void*)&k_stockham_cluster<N, K, -1, TPB, PS, Rs...>,
                        (const void*)&k_stockham_cluster<N, K, +1, TPB, PS, Rs...>};
 }
@@ -152,6 +167,11 @@ const RowsVariant kCluster[] = {
 };
 
 }  // namespace
+
+// Lengths whose default plan is the cluster kernel (variant 0) rather than Eq. 2 as two passes:
+// where it measured faster on GB300.  N = 8192 on a pair of CTAs: 1.07x the two passes; the other
+// K = 2 lengths 0.90-0.98x, K = 4 and 8 at most 0.76x.
+bool cluster_is_default(int64_t n) { return n == 8192; }
 
 int cluster_variants_for(int64_t n, const RowsVariant** out, int max_out) {
     int found = 0;

@@ -36,6 +36,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "codelets.cuh"
 #include "gbfft.h"
@@ -80,6 +81,14 @@ struct ContigIO {
     __device__ __forceinline__ C ld(int t, int n) const { return in[t * N + n]; }
     __device__ __forceinline__ void st(int t, int n, C v) const { out[t * N + n] = v; }
 };
+// An IO whose stores land in the same shared memory the last stage reads
+// declares `static constexpr bool kSyncBeforeStore = true`: the stage engine
+// then synchronises between the last stage's reads and its stores.
+template <class IO, class = void>
+struct SyncBeforeStore : std::false_type {};
+template <class IO>
+struct SyncBeforeStore<IO, std::void_t<decltype(IO::kSyncBeforeStore)>> : std::bool_constant<IO::kSyncBeforeStore> {};
+
 // IndexedIO: row t starts at complex element off[t] of both buffers.
 template <int N, class C = float2>
 struct IndexedIO {
@@ -210,6 +219,7 @@ __device__ __forceinline__ void run_stages_t(C (&v)[E], const IO& io, C* sm, con
     }
     if constexpr (LAST) {
         static_assert(L * R == N, "schedule must multiply to N");
+        if constexpr (SyncBeforeStore<IO>::value) __syncthreads();
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int B = tid + u * TPB;

@@ -57,7 +57,7 @@ def test_cluster_in_place_and_two_pass_agree(n):
     assert info["k_outer"] == 1 and info["workspace_bytes"] == 0  # one pass, no workspace
     b, _ = run(x, -1, variant=0, inplace=True)
     assert np.array_equal(a, b)
-    c, info2 = run(x, -1)  # the default above 4096: Eq. 2 as two passes
+    c, info2 = run(x, -1, k_outer=0)  # Eq. 2 as two passes with the planner's split
     assert info2["k_outer"] > 1
     assert row_rel_l2(a, c).max() <= 2 * tol_fp32(n)
 
@@ -77,3 +77,15 @@ def test_cluster_full_size_sampled_rows(n):
     rows = np.concatenate([synth.sample_rows(SEED, batch, 64), [batch - 1]])
     y = d_out.view(batch, 2 * n)[torch.from_numpy(rows).cuda()].cpu().numpy().view(np.complex64)
     check(y, flat.reshape(batch, n)[rows], -1)
+
+
+def test_default_plan_above_4096():
+    """The cluster kernel is the default where it measured faster (N = 8192);
+    other lengths above 4096 default to Eq. 2 as two passes."""
+    from paper_2207_06803_gb300 import gbfft
+    for n, one_pass in ((8192, True), (5120, False), (16384, False), (65536, False)):
+        with gbfft.Plan(n, 4, -1) as p:
+            k, _ = gbfft.gbfft_plan_factors(p.handle)
+            assert (k == 1) == one_pass, (n, k)
+            if one_pass:
+                assert gbfft.gbfft_variant_kind(n, p.info()["variant"]) == 4

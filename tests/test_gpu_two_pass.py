@@ -60,8 +60,8 @@ def test_beyond_single_pass_range(n):
 
 def test_two_pass_in_place():
     x = synth.uniform_batch(SEED, 8192, 7)
-    a, _ = run(x, -1)
-    b, _ = run(x, -1, inplace=True)
+    a, _ = run(x, -1, k_outer=0)
+    b, _ = run(x, -1, k_outer=0, inplace=True)
     assert np.array_equal(a, b)
 
 
@@ -85,7 +85,7 @@ def test_full_size_sampled_rows(n):
     flat = synth.uniform_flat(SEED, 0, total)
     d_in = torch.from_numpy(flat.view(np.float32)).cuda()
     d_out = torch.empty_like(d_in)
-    with gbfft.Plan(n, batch, -1) as p:
+    with gbfft.Plan(n, batch, -1, k_outer=0) as p:  # Eq. 2 as two passes, the planner's split
         p.execute(d_in, d_out)
         torch.cuda.synchronize()
     rows = synth.sample_rows(SEED + n, batch, 256)
