@@ -58,7 +58,7 @@ struct ColumnIO {
 };
 
 template <int N, int K, int S, int TPB, int PS, int... Rs>
-__global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB)
+__global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, 1024 / TPB)
     k_stockham_cluster(const float2* in, float2* out, const float2* __restrict__ tw, long long batch) {
     constexpr int M = N / K;
     constexpr int E = capacity_of_r<M, 1, TPB, Rs...>();
@@ -155,14 +155,22 @@ const RowsVariant kCluster[] = {
     GBFFT_CLUSTER(7168, 2, 224, 4, 7, 16, 16, 2),
     GBFFT_CLUSTER(8192, 2, 256, 4, 16, 16, 16),
     GBFFT_CLUSTER(8192, 4, 128, 4, 16, 16, 8),
-    GBFFT_CLUSTER(10240, 4, 160, 5, 5, 16, 16, 2),
+    GBFFT_CLUSTER(10240, 2, 320, 4, 5, 16, 16, 4),  // CTA pairs on 5120-8192-long columns first: fewer
+    GBFFT_CLUSTER(10240, 4, 160, 5, 5, 16, 16, 2),  // CTAs per row measured faster (N = 16384: K = 2 at
+    GBFFT_CLUSTER(12288, 2, 384, 4, 3, 16, 16, 8),  // 0.87x the two passes, K = 4 at 0.63x)
     GBFFT_CLUSTER(12288, 4, 192, 4, 3, 16, 16, 4),
+    GBFFT_CLUSTER(14336, 2, 448, 4, 7, 16, 16, 4),
     GBFFT_CLUSTER(14336, 4, 224, 4, 7, 16, 16, 2),
+    GBFFT_CLUSTER(16384, 2, 512, 4, 16, 16, 16, 2),
     GBFFT_CLUSTER(16384, 4, 256, 4, 16, 16, 16),
     GBFFT_CLUSTER(16384, 8, 128, 4, 16, 16, 8),
+    GBFFT_CLUSTER(20480, 4, 320, 4, 5, 16, 16, 4),
     GBFFT_CLUSTER(20480, 8, 160, 5, 5, 16, 16, 2),
+    GBFFT_CLUSTER(24576, 4, 384, 4, 3, 16, 16, 8),
     GBFFT_CLUSTER(24576, 8, 192, 4, 3, 16, 16, 4),
+    GBFFT_CLUSTER(28672, 4, 448, 4, 7, 16, 16, 4),
     GBFFT_CLUSTER(28672, 8, 224, 4, 7, 16, 16, 2),
+    GBFFT_CLUSTER(32768, 4, 512, 4, 16, 16, 16, 2),
     GBFFT_CLUSTER(32768, 8, 256, 4, 16, 16, 16),
 };
 
