@@ -288,9 +288,12 @@ gbfft_status gbfft_formula_check(const char *formula, int64_t *n, int *leaves, i
                                  int64_t *k_outer, char *err, size_t err_len);
 
 /*
- * The factorisation a formula states at its top level: 0 Eq. 2 (or a single
- * DFT(N)), 1 Eq. 2's transpose (decimation in frequency), 2 Pease's form; -1
- * when gbfft_formula_check rejects it.  Host only.
+ * The factorisation a formula (Table I vocabulary) states at its top level:
+ * 0 Eq. 2 (or a single DFT(N)), 1 Eq. 2's transpose (decimation in
+ * frequency), 2 Pease's constant-geometry form (named in Sec. II; written out
+ * above); -1 when gbfft_formula_check rejects it (NULL or malformed text
+ * included).  `formula` is caller-owned UTF-8 text, only read.  Host only: no
+ * CUDA call.
  */
 int gbfft_formula_form(const char *formula);
 
