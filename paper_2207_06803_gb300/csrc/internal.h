@@ -150,7 +150,9 @@ int rows_variants_for(int64_t n, const RowsVariant** out, int max_out);
 // One-pass cluster variants for 4096 < n <= 32768 (cluster.cu); their radix
 // list is the column schedule followed by the cluster size K.
 int cluster_variants_for(int64_t n, const RowsVariant** out, int max_out);
-bool cluster_is_default(int64_t n);  // the default plan for n is the cluster kernel (variant 0)
+bool cluster_is_default(int64_t n);
+// The planner's Eq. 2 split N = K * M for the two-pass form (k_req > 0: that K, if valid); false if none.
+bool choose_split(int64_t n, int64_t k_req, int64_t* k_out, int64_t* m_out);  // the default plan for n is the cluster kernel (variant 0)
 // The one-pass variants of a length: single-CTA rows kernels, else cluster kernels.
 int onepass_variants_for(int64_t n, const RowsVariant** out, int max_out);
 // Twiddle tables of a cluster variant: the column's stage blocks, then D^N_M.

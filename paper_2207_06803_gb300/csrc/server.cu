@@ -179,14 +179,7 @@ gbfft_status get_plan(Server* s, int64_t n, int dir, ServerPlan** out) {
         if (cudaMalloc(&sp.tw, sizeof(float2) * (size_t)std::max(cnt, 1)) != cudaSuccess) return GBFFT_ERR_OOM;
         if (launch_stage_twiddles(sp.tw, n, sp.rv->radix, sp.rv->nstages, s->tstream) != cudaSuccess) return GBFFT_ERR_CUDA;
     } else {
-        static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
-        for (int64_t m : pref)
-            if (n % m == 0 && (n / m) % 16 == 0 && cols_variant_for(m) && cols_variant_for(n / m)) {
-                sp.m = m;
-                sp.k = n / m;
-                break;
-            }
-        if (sp.m == 0) return GBFFT_ERR_UNSUPPORTED_SIZE;
+        if (!choose_split(n, 0, &sp.k, &sp.m)) return GBFFT_ERR_UNSUPPORTED_SIZE;
         sp.two_pass = true;
         sp.cm = cols_variant_for(sp.m);
         sp.ck = cols_variant_for(sp.k);
@@ -453,13 +446,8 @@ gbfft_status server_submit(Server* s, int64_t n, int64_t batch, int direction, c
                            uint64_t* ticket, const Clock::time_point* arrival = nullptr) {
     if (!s || !in || !out || !ticket || batch < 1 || n < 1) return GBFFT_ERR_INVALID_ARG;
     if (direction != GBFFT_FORWARD && direction != GBFFT_INVERSE) return GBFFT_ERR_INVALID_ARG;
-    if (rows_variants_for(n, nullptr, 0) == 0) {
-        bool ok = false;
-        static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
-        for (int64_t m : pref)
-            if (n % m == 0 && (n / m) % 16 == 0 && cols_variant_for(m) && cols_variant_for(n / m)) ok = true;
-        if (!ok) return GBFFT_ERR_UNSUPPORTED_SIZE;
-    }
+    int64_t kk = 0, mm = 0;
+    if (rows_variants_for(n, nullptr, 0) == 0 && !choose_split(n, 0, &kk, &mm)) return GBFFT_ERR_UNSUPPORTED_SIZE;
     if (slot_bytes(n, batch, needs_two_pass(n)) + 256 > s->budget) return GBFFT_ERR_BUDGET;
     auto r = std::make_unique<Request>();
     r->n = n;

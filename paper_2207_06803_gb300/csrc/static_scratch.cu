@@ -49,17 +49,7 @@ cudaError_t scratch_address(int dev, void** out) {
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
-bool split_for(int64_t n, int64_t* k_out, int64_t* m_out) {
-    static const int64_t pref[] = {128, 64, 256, 96, 112, 80, 48, 32, 512};
-    for (int64_t m : pref) {
-        if (n % m == 0 && cols_variant_for(m) && cols_variant_for(n / m)) {
-            *k_out = n / m;
-            *m_out = m;
-            return true;
-        }
-    }
-    return false;
-}
+bool split_for(int64_t n, int64_t* k_out, int64_t* m_out) { return choose_split(n, 0, k_out, m_out); }
 
 }  // namespace
 }  // namespace gbfft
