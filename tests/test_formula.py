@@ -303,6 +303,7 @@ def test_formula_form_codes():
     assert gbfft.gbfft_formula_form(render(eq2_transposed(dft(4), dft(8)))) == 1
     assert gbfft.gbfft_formula_form(render(pease(4, 3))) == 2
     assert gbfft.gbfft_formula_form("I(4)") == -1
+    assert gbfft.lib().gbfft_formula_form(None) == -1
 
 
 # -- formula-driven plans on the GPU -----------------------------------------
