@@ -269,6 +269,44 @@ def test_pease_form_is_dft_densely(r, t):
         assert gbfft.gbfft_formula_form(render(f)) == 2
 
 
+def pease_by_index(x, r, sign=-1):
+    """Pease's form in the index terms the kernel uses (z_0 = digit-reversed x;
+    stage s: butterfly j takes z[j r + q] * w_{r^s}^(q floor(j / r^(t-s))),
+    applies DFT_r and writes z'[p N/r + j]), in complex128."""
+    n = x.size
+    t = round(math.log(n, r))
+    nr = n // r
+
+    def rev(v, m):
+        y = 0
+        for _ in range(m):
+            y, v = y * r + v % r, v // r
+        return y
+
+    z = np.array([x[rev(i, t)] for i in range(n)], dtype=np.complex128)
+    f = np.exp(sign * 2j * np.pi * np.outer(np.arange(r), np.arange(r)) / r)
+    for s in range(1, t + 1):
+        zn = np.empty_like(z)
+        for j in range(nr):
+            k = j // r ** (t - s)
+            a = z[j * r + np.arange(r)] * np.exp(sign * 2j * np.pi * np.arange(r) * k / r ** s)
+            zn[np.arange(r) * nr + j] = f @ a
+        z = zn
+    return z
+
+
+@pytest.mark.parametrize("r,t", [(2, 5), (4, 3), (8, 2), (8, 3), (16, 2), (3, 3), (5, 2)])
+def test_pease_index_form_is_the_dft(r, t):
+    """Pins the kernel's index form of Pease's stages (both directions) to the oracle's direct DFT."""
+    import oracle
+    n = r ** t
+    x = synth.uniform_batch(synth.DEFAULT_SEED + n, n, 2).astype(np.complex128)
+    for sign in (-1, 1):
+        ref = oracle.dft_naive(x, sign)
+        got = np.stack([pease_by_index(row, r, sign) for row in x])
+        assert np.max(np.abs(got - ref)) <= 1e-12 * n, (r, t, sign)
+
+
 def pease_mutations(r, t):
     """Plausible mistakes in Pease's form (t >= 3): each denotes another matrix."""
     n = r ** t
