@@ -57,7 +57,9 @@ struct ColumnIO {
     }
 };
 
-template <int N, int K, int S, int TPB, int PS, int... Rs>
+// VA: phase A by groups of K consecutive elements (16-byte loads; each destination column receives
+// consecutive slots from consecutive threads), else element by element (8-byte loads at stride TPB).
+template <int N, int K, int S, int TPB, int PS, bool VA, int... Rs>
 __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, 1024 / TPB)
     k_stockham_cluster(const float2* in, float2* out, const float2* __restrict__ tw, long long batch) {
     constexpr int M = N / K;
@@ -74,11 +76,37 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, 1024 / TPB)
     (void)batch;
 
     // A. block k of the row -> columns (Pi^N_K); all loads are issued before the remote stores.
-    // Another CTA's shared memory may be written only once that CTA is running: the cluster
-    // barrier below is passed only when every CTA of the cluster has started.  (Staging the block
-    // locally to send 16-byte pieces measured slower than these 8-byte stores.)
+    // Element k*M + i goes to column (k*M + i) mod K, slot (k*M + i) div K.  Another CTA's shared
+    // memory may be written only once that CTA is running: the cluster barrier below is passed
+    // only when every CTA of the cluster has started.
     const float2* x = in + row * N + (long long)k * M;
-    {
+    if constexpr (VA) {
+        // thread g takes the K consecutive elements g*K + q: element q goes to column q, slot
+        // k*M/K + g, so for each q consecutive threads write consecutive slots of one column
+        constexpr int JG = M / K;     // groups of K elements in the block
+        constexpr int NG = JG / TPB;  // groups per thread
+        static_assert(JG % TPB == 0 && K % 2 == 0, "the block splits into whole groups per thread");
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        float2 a[NG][K];
+#pragma unroll
+        for (int e = 0; e < NG; ++e) {
+            const int g = tid + e * TPB;
+#pragma unroll
+            for (int h = 0; h < K / 2; ++h) {
+                const float4 w = x4[g * (K / 2) + h];
+                a[e][2 * h] = make_float2(w.x, w.y);
+                a[e][2 * h + 1] = make_float2(w.z, w.w);
+            }
+        }
+        cluster_sync_relaxed();  // every CTA of the cluster runs: its shared memory may be written
+        const int base = spad<PS>(k * JG + tid);
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            float2* d = cluster.map_shared_rank(col + base, q);
+#pragma unroll
+            for (int e = 0; e < NG; ++e) d[spad<PS>(k * JG + tid + e * TPB) - base] = a[e][q];
+        }
+    } else {
         constexpr int NE = M / TPB;
         float2 a[NE];
 #pragma unroll
@@ -129,7 +157,7 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, 1024 / TPB)
     cluster_sync_relaxed();  // no CTA leaves while the others still read its column
 }
 
-template <int N, int K, int TPB, int PS, int... Rs>
+template <int N, int K, int TPB, int PS, bool VA, int... Rs>
 RowsVariant make_cluster_variant() {
     constexpr int M = N / K;
     return RowsVariant{kRowsCluster,
@@ -141,37 +169,39 @@ RowsVariant make_cluster_variant() {
                        (int)sizeof...(Rs) + 1,
                        {Rs..., K},
                        (int)(smem_elems<1, M, PS>() * sizeof(float2)),
-                       (const void*)&k_stockham_cluster<N, K, -1, TPB, PS, Rs...>,
-                       (const void*)&k_stockham_cluster<N, K, +1, TPB, PS, Rs...>};
+                       (const void*)&k_stockham_cluster<N, K, -1, TPB, PS, VA, Rs...>,
+                       (const void*)&k_stockham_cluster<N, K, +1, TPB, PS, VA, Rs...>};
 }
 
-#define GBFFT_CLUSTER(N, K, TPB, PS, ...) make_cluster_variant<N, K, TPB, PS, __VA_ARGS__>()
+#define GBFFT_CLUSTER(N, K, TPB, PS, VA, ...) make_cluster_variant<N, K, TPB, PS, VA, __VA_ARGS__>()
 
 // Column schedules are the single-pass ones of the same lengths; the radix
-// list of a variant is the column schedule followed by K.
+// list of a variant is the column schedule followed by K.  The grouped phase A
+// (VA) measured faster everywhere but on N = 8192 and 16384 with K = 2, whose
+// kernels spill with it (8192: 3.31 against 3.57 TB/s).
 const RowsVariant kCluster[] = {
-    GBFFT_CLUSTER(5120, 2, 160, 5, 5, 16, 16, 2),
-    GBFFT_CLUSTER(6144, 2, 192, 4, 3, 16, 16, 4),
-    GBFFT_CLUSTER(7168, 2, 224, 4, 7, 16, 16, 2),
-    GBFFT_CLUSTER(8192, 2, 256, 4, 16, 16, 16),
-    GBFFT_CLUSTER(8192, 4, 128, 4, 16, 16, 8),
-    GBFFT_CLUSTER(10240, 2, 320, 4, 5, 16, 16, 4),  // CTA pairs on 5120-8192-long columns first: fewer
-    GBFFT_CLUSTER(10240, 4, 160, 5, 5, 16, 16, 2),  // CTAs per row measured faster (N = 16384: K = 2 at
-    GBFFT_CLUSTER(12288, 2, 384, 4, 3, 16, 16, 8),  // 0.87x the two passes, K = 4 at 0.63x)
-    GBFFT_CLUSTER(12288, 4, 192, 4, 3, 16, 16, 4),
-    GBFFT_CLUSTER(14336, 2, 448, 4, 7, 16, 16, 4),
-    GBFFT_CLUSTER(14336, 4, 224, 4, 7, 16, 16, 2),
-    GBFFT_CLUSTER(16384, 2, 512, 4, 16, 16, 16, 2),
-    GBFFT_CLUSTER(16384, 4, 256, 4, 16, 16, 16),
-    GBFFT_CLUSTER(16384, 8, 128, 4, 16, 16, 8),
-    GBFFT_CLUSTER(20480, 4, 320, 4, 5, 16, 16, 4),
-    GBFFT_CLUSTER(20480, 8, 160, 5, 5, 16, 16, 2),
-    GBFFT_CLUSTER(24576, 4, 384, 4, 3, 16, 16, 8),
-    GBFFT_CLUSTER(24576, 8, 192, 4, 3, 16, 16, 4),
-    GBFFT_CLUSTER(28672, 4, 448, 4, 7, 16, 16, 4),
-    GBFFT_CLUSTER(28672, 8, 224, 4, 7, 16, 16, 2),
-    GBFFT_CLUSTER(32768, 4, 512, 4, 16, 16, 16, 2),
-    GBFFT_CLUSTER(32768, 8, 256, 4, 16, 16, 16),
+    GBFFT_CLUSTER(5120, 2, 160, 5, true, 5, 16, 16, 2),
+    GBFFT_CLUSTER(6144, 2, 192, 4, true, 3, 16, 16, 4),
+    GBFFT_CLUSTER(7168, 2, 224, 4, true, 7, 16, 16, 2),
+    GBFFT_CLUSTER(8192, 2, 256, 4, false, 16, 16, 16),
+    GBFFT_CLUSTER(8192, 4, 128, 4, true, 16, 16, 8),
+    GBFFT_CLUSTER(10240, 2, 320, 4, true, 5, 16, 16, 4),  // CTA pairs on 5120-8192-long columns first: fewer
+    GBFFT_CLUSTER(10240, 4, 160, 5, true, 5, 16, 16, 2),  // CTAs per row measured faster (N = 16384: K = 2 at
+    GBFFT_CLUSTER(12288, 2, 384, 4, true, 3, 16, 16, 8),  // 0.87x the two passes, K = 4 at 0.63x)
+    GBFFT_CLUSTER(12288, 4, 192, 4, true, 3, 16, 16, 4),
+    GBFFT_CLUSTER(14336, 2, 448, 4, true, 7, 16, 16, 4),
+    GBFFT_CLUSTER(14336, 4, 224, 4, true, 7, 16, 16, 2),
+    GBFFT_CLUSTER(16384, 2, 512, 4, false, 16, 16, 16, 2),
+    GBFFT_CLUSTER(16384, 4, 256, 4, true, 16, 16, 16),
+    GBFFT_CLUSTER(16384, 8, 128, 4, true, 16, 16, 8),
+    GBFFT_CLUSTER(20480, 4, 320, 4, true, 5, 16, 16, 4),
+    GBFFT_CLUSTER(20480, 8, 160, 5, true, 5, 16, 16, 2),
+    GBFFT_CLUSTER(24576, 4, 384, 4, true, 3, 16, 16, 8),
+    GBFFT_CLUSTER(24576, 8, 192, 4, true, 3, 16, 16, 4),
+    GBFFT_CLUSTER(28672, 4, 448, 4, true, 7, 16, 16, 4),
+    GBFFT_CLUSTER(28672, 8, 224, 4, true, 7, 16, 16, 2),
+    GBFFT_CLUSTER(32768, 4, 512, 4, true, 16, 16, 16, 2),
+    GBFFT_CLUSTER(32768, 8, 256, 4, true, 16, 16, 16),
 };
 
 }  // namespace
