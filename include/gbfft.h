@@ -342,7 +342,8 @@ gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void 
  * Autotuner for a ragged plan: tries both queue orders, then for each length,
  * heaviest first, the tile split 1, 2, 4, 8 (rows per item = (8192/n)/split,
  * at most 512), each candidate radix schedule of the length and the shared
- * memory padding, timing the whole persistent launch on `in`/`out` (median of
+ * memory padding,
+ * timing the whole persistent launch on `in`/`out` (median of
  * `reps` after one warm-up; `out` is overwritten), keeping each change that
  * makes it faster.  *best_ms (may be NULL) receives the best median time.
  * Synchronous.
@@ -446,9 +447,13 @@ gbfft_status gbfft_server_destroy(gbfft_server srv);
  * call; `in`/`out` are caller-owned device pointers as for gbfft_execute.
  * Limits: 8*n*batch bytes of workspace plus the tables (8*n bytes and the
  * stage blocks, each rounded up to 256 bytes) must fit in the 64 MiB, else
- * GBFFT_ERR_BUDGET; n must have a two-pass split (UNSUPPORTED_SIZE).  The
- * first call on a device looks up the array's device address for that device
- * (a one-time set-up); make that first call before any stream capture.  All
+ * GBFFT_ERR_BUDGET (checked before any byte count is formed, so a huge batch
+ * cannot wrap it); n must have a two-pass split (UNSUPPORTED_SIZE).  The
+ * array's device address belongs to the CUDA context that loaded the library's
+ * module: the first call on a device looks it up in the current context, and
+ * every later call whose stream is not capturing looks it up again, so a
+ * device reset or another current context never leaves a stale address in
+ * use.  Make the first call on each device before any stream capture.  All
  * calls share the array and it keeps the last call's contents: calls that
  * overlap on the GPU race and corrupt each other, so serialise them.  The call
  * makes no cudaMalloc/cudaFree.  Errors: INVALID_ARG, ALIGNMENT, OVERLAP,

@@ -15,7 +15,10 @@
 // start at zero, because each call writes every table entry and every
 // workspace element before reading it.  Calls that overlap on the GPU (two
 // streams, or two host threads) race on the array and corrupt each other's
-// results; serialise them.
+// results; serialise them.  The array's device address is looked up in the
+// current context by every call whose stream is not capturing (the address
+// belongs to the context that loaded the module).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -30,20 +33,61 @@ constexpr size_t kGbfftStaticScratchBytes = size_t(64) << 20;  // 64 MiB
 __device__ __align__(256) unsigned char g_static_scratch[kGbfftStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+// Last address found per device, with the context it belongs to.  Only a call
+// made while its stream is capturing uses it (see scratch_address).
+struct ScratchSlot {
+    CUcontext ctx = nullptr;
+    void* addr = nullptr;
+};
+ScratchSlot g_scratch_slot[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Device address of the array for device `dev` (current).  Host code cannot
-// use the symbol itself: on the host it names a stand-in, not device memory.
-cudaError_t scratch_address(int dev, void** out) {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+// The driver's cuCtxGetCurrent, reached through the runtime (the library does
+// not link the driver library itself, so it still loads on a host without one).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+
+bool current_context(CUcontext* ctx) {
+    if (!g_ctx_get_current) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
     }
-    *out = g_scratch_addr[dev];
+    *ctx = nullptr;
+    return g_ctx_get_current(ctx) == CUDA_SUCCESS && *ctx != nullptr;
+}
+
+// Device address of the array in the current context of device `dev`.  Host
+// code cannot use the symbol itself: on the host it names a stand-in, not
+// device memory.  The address belongs to the context that loaded the module,
+// so a call whose stream is not capturing looks it up afresh each time (a
+// device reset or a different current context then cannot leave a stale
+// address behind); a call whose stream is capturing reuses the address the
+// last uncaptured call found in the same context, and fails if there is none.
+cudaError_t scratch_address(int dev, cudaStream_t s, void** out) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    ScratchSlot& slot = g_scratch_slot[dev];
+    if (cs == cudaStreamCaptureStatusNone) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        CUcontext ctx = nullptr;
+        if (!current_context(&ctx)) return cudaErrorDeviceUninitialized;
+        slot.ctx = ctx;
+        slot.addr = p;
+        *out = p;
+        return cudaSuccess;
+    }
+    CUcontext ctx = nullptr;
+    if (!current_context(&ctx) || ctx != slot.ctx || !slot.addr)
+        return cudaErrorDeviceUninitialized;
+    *out = slot.addr;
     return cudaSuccess;
 }
 
@@ -63,6 +107,8 @@ extern "C" gbfft_status gbfft_execute_twopass_noalloc(int64_t n, int64_t batch, 
     if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u)) return GBFFT_ERR_ALIGNMENT;
     int64_t k = 0, m = 0;
     if (!split_for(n, &k, &m)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    // Bound batch before multiplying, so that the byte count cannot wrap.
+    if (batch > (int64_t)(kGbfftStaticScratchBytes / (sizeof(float2) * (size_t)n))) return GBFFT_ERR_BUDGET;
     const size_t bytes = sizeof(float2) * (size_t)n * (size_t)batch;
     if (in != out) {
         const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
@@ -80,7 +126,7 @@ extern "C" gbfft_status gbfft_execute_twopass_noalloc(int64_t n, int64_t batch, 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GBFFT_ERR_CUDA;
     void* base = nullptr;
-    if (scratch_address(dev, &base) != cudaSuccess) return GBFFT_ERR_CUDA;
+    if (scratch_address(dev, (cudaStream_t)cuda_stream, &base) != cudaSuccess) return GBFFT_ERR_CUDA;
     if (prepare_cols(*cm) != cudaSuccess || prepare_cols(*ck) != cudaSuccess) return GBFFT_ERR_CUDA;
 
     char* p = (char*)base;
