@@ -14,6 +14,10 @@ The arithmetic lives in ``oracle.c`` (plain C, FP64):
 * :func:`fft_eq2`    -- the recursion of Eq. 2,
   ``DFT_N = (DFT_K (x) I_M) D^N_M (I_K (x) DFT_M) Pi^N_K``.
 
+:func:`dft_nd` composes them: the multi-dimensional DFT of row-major arrays,
+``DFT_{d0} (x) ... (x) DFT_{d(r-1)}`` (Table I's Kronecker product applied to
+whole transforms), one axis at a time.
+
 ``sign`` is the exponent sign: -1 forward, +1 unnormalised inverse, so that
 ``inverse(forward(x)) == N * x``.
 """
@@ -98,3 +102,21 @@ def dft(x, sign: int = FORWARD, nthreads: int = 1) -> np.ndarray:
     if n <= 1024:
         return dft_naive(x, sign, nthreads)
     return fft_eq2(x, sign, nthreads)
+
+
+def dft_nd(x, sign: int = FORWARD, nthreads: int = 1) -> np.ndarray:
+    """Multi-dimensional DFT of each item of a batch: x has shape
+    (batch, d0, ..., d(r-1)), row-major.  The Kronecker product
+    DFT_{d0} (x) ... (x) DFT_{d(r-1)} (Table I's operator on whole transforms)
+    factors as (DFT_{d0} (x) I) (I (x) DFT_{d1} (x) I) ... , so the result is
+    the 1-D transform of Sec. II along every axis in turn; each 1-D step is
+    :func:`dft`.  The order of the axes does not matter (the factors commute)."""
+    y = np.asarray(x, np.complex128)
+    if y.ndim < 2:
+        raise ValueError("expected (batch, d0, ..., d(r-1))")
+    for ax in range(1, y.ndim):
+        moved = np.moveaxis(y, ax, -1)
+        shape = moved.shape
+        out = dft(np.ascontiguousarray(moved).reshape(-1, shape[-1]), sign, nthreads).reshape(shape)
+        y = np.moveaxis(out, -1, ax)
+    return np.ascontiguousarray(y)

@@ -1,8 +1,7 @@
 """Multi-dimensional transforms DFT_{d0} ⊗ ... ⊗ DFT_{d(r-1)} (Table I's Kronecker
-product applied to whole transforms) through the C ABI, against the oracle
-applied axis by axis; that separable reference is itself pinned to the direct
-multi-dimensional DFT sum on small shapes."""
-import itertools
+product applied to whole transforms) through the C ABI, against the oracle's
+``dft_nd`` (pinned to the direct multi-dimensional DFT sum in
+``test_oracle_pins.py``)."""
 import math
 
 import numpy as np
@@ -13,39 +12,6 @@ from helpers import ncpu, row_rel_l2, tol_fp32
 from paper_2207_06803_gb300 import synth
 
 SEED = synth.DEFAULT_SEED
-
-
-def reference_nd(x, direction):
-    """x: (batch, d0, ..., d(r-1)); the 1-D oracle along every axis in turn."""
-    y = np.asarray(x, np.complex128)
-    for ax in range(1, y.ndim):
-        moved = np.moveaxis(y, ax, -1)
-        shape = moved.shape
-        out = oracle.dft(moved.reshape(-1, shape[-1]), direction, nthreads=ncpu()).reshape(shape)
-        y = np.moveaxis(out, -1, ax)
-    return y
-
-
-def direct_nd(x, direction):
-    """The multi-dimensional DFT by its definition: one sum over every index tuple."""
-    dims = x.shape
-    out = np.zeros(dims, np.complex128)
-    for k in itertools.product(*[range(d) for d in dims]):
-        acc = 0j
-        for n in itertools.product(*[range(d) for d in dims]):
-            phase = sum(ki * ni / d for ki, ni, d in zip(k, n, dims))
-            acc += x[n] * np.exp(direction * 2j * np.pi * phase)
-        out[k] = acc
-    return out
-
-
-@pytest.mark.parametrize("dims", [(3, 4), (2, 5), (2, 3, 4), (4, 1, 3)])
-@pytest.mark.parametrize("direction", [-1, 1])
-def test_separable_reference_is_the_nd_definition(dims, direction):
-    rng = np.random.default_rng(7)
-    x = rng.standard_normal(dims) + 1j * rng.standard_normal(dims)
-    got = reference_nd(x[None], direction)[0]
-    assert np.max(np.abs(got - direct_nd(x, direction))) < 1e-12 * math.prod(dims)
 
 
 def run_nd(x, direction, inplace=False):
@@ -71,7 +37,7 @@ def test_nd_matches_the_oracle(dims, direction):
     batch = max(1, min(3, (1 << 22) // total))
     x = synth.uniform_flat(SEED + total, 0, batch * total).reshape((batch,) + dims)
     y = run_nd(x, direction)
-    ref = reference_nd(x, direction)
+    ref = oracle.dft_nd(x, direction, nthreads=ncpu())
     err = row_rel_l2(y.reshape(batch, -1), ref.reshape(batch, -1))
     tol = sum(tol_fp32(d) for d in dims)  # one FP32 transform per axis
     assert np.all(np.isfinite(err)) and err.max() <= tol, (dims, err.max(), tol)

@@ -350,3 +350,44 @@ def test_threaded_matches_single_thread():
 def test_invalid_arguments_rejected():
     with pytest.raises(ValueError):
         oracle.fft_radix2(np.zeros(12, complex))
+
+
+def direct_nd(x, sign):
+    """The multi-dimensional DFT by its definition: one sum over every index
+    tuple, y[k] = sum_n x[n] exp(sign 2 pi i sum_a k_a n_a / d_a)."""
+    import itertools
+    dims = x.shape
+    out = np.zeros(dims, np.complex128)
+    for k in itertools.product(*[range(d) for d in dims]):
+        acc = 0j
+        for n in itertools.product(*[range(d) for d in dims]):
+            phase = sum(ki * ni / d for ki, ni, d in zip(k, n, dims))
+            acc += x[n] * np.exp(sign * 2j * np.pi * phase)
+        out[k] = acc
+    return out
+
+
+@pytest.mark.parametrize("dims", [(3, 4), (2, 5), (2, 3, 4), (4, 1, 3)])
+@pytest.mark.parametrize("sign", [FWD, INV])
+def test_dft_nd_is_the_multidimensional_definition(dims, sign):
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(dims) + 1j * rng.standard_normal(dims)
+    got = oracle.dft_nd(x[None], sign)[0]
+    assert np.max(np.abs(got - direct_nd(x, sign))) < 1e-12 * math.prod(dims)
+
+
+def test_dft_nd_planted_mistakes_fail_the_definition():
+    """Plausible slips in an axis-by-axis multi-dimensional DFT (an axis
+    skipped, one axis transformed with the opposite sign, the axes' lengths
+    swapped on a non-square shape) each disagree with the direct sum."""
+    dims = (3, 4)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(dims) + 1j * rng.standard_normal(dims)
+    want = direct_nd(x, FWD)
+    skipped = oracle.dft(x, FWD)                                  # last axis only
+    wrong_sign = oracle.dft(oracle.dft(x.T, INV).T, FWD)          # axis 0 inverse
+    swapped = oracle.dft(oracle.dft(x.reshape(4, 3), FWD).T, FWD).T.reshape(dims)
+    for bad in (skipped, wrong_sign, swapped):
+        assert np.max(np.abs(bad - want)) > 1e-3
+    right = oracle.dft(oracle.dft(x, FWD).T, FWD).T
+    assert np.max(np.abs(right - want)) < 1e-12
