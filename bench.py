@@ -749,12 +749,18 @@ def run_ragged(args):
            "points": total, "algorithmic_bytes": nbytes}
     with gbfft.RaggedPlan(sizes, offs, -1) as rp:
         ms0 = _time_ms(torch, lambda: rp.execute(d_in, d_out, stream), reps, stream)
+        # the same queue with every length on the run-time engine (schedules read from descriptors)
+        gbfft.gbfft_ragged_set_engine(rp.handle, 0, 0)
+        ms_rt = _time_ms(torch, lambda: rp.execute(d_in, d_out, stream), reps, stream)
+        gbfft.gbfft_ragged_set_engine(rp.handle, 0, 1)
+        res["ragged_graph_runtime_engine_us"] = 1e3 * ms_rt
         tuned = rp.autotune(d_in, d_out, reps=5)
         ms1 = _time_ms(torch, lambda: rp.execute(d_in, d_out, stream), reps, stream)
         res["ragged_graph_default_us"] = 1e3 * ms0
         res["ragged_graph_tuned_us"] = 1e3 * ms1
         res["ragged_gbs"] = nbytes / (ms1 * 1e-3) / 1e9
         res["items"] = rp.num_items()
+        res["engines"] = {str(n): gbfft.gbfft_ragged_engine(rp.handle, int(n)) for n in sorted(set(sizes.tolist()))}
         res["queue_order"] = gbfft.gbfft_ragged_queue_order(rp.handle)
         res["tile_splits"] = {str(n): gbfft.gbfft_ragged_tile_split(rp.handle, int(n))
                               for n in sorted(set(sizes.tolist()))}

@@ -340,9 +340,9 @@ gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void 
 
 /*
  * Autotuner for a ragged plan: tries both queue orders, then for each length,
- * heaviest first, the tile split 1, 2, 4, 8 (rows per item = (8192/n)/split,
- * at most 512), each candidate radix schedule of the length and the shared
- * memory padding,
+ * heaviest first, the compiled or the run-time engine (gbfft_ragged_set_engine),
+ * the tile split 1, 2, 4, 8 (rows per item = (rows of the engine's tile)/split),
+ * and, on the run-time engine, each candidate radix schedule of the length,
  * timing the whole persistent launch on `in`/`out` (median of
  * `reps` after one warm-up; `out` is overwritten), keeping each change that
  * makes it faster.  *best_ms (may be NULL) receives the best median time.
@@ -363,9 +363,27 @@ int gbfft_ragged_schedule(gbfft_plan p, int64_t n, int *radices);
 /* Number of work items in the plan's queue (-1 if not a ragged plan). */
 int64_t gbfft_ragged_num_items(gbfft_plan p);
 
-/* The tile split the plan uses for length n (rows per item =
- * (8192/n)/split, at most 512), 0 if n is not in this plan. */
+/* The tile split the plan uses for length n (rows per item = (rows of the
+ * tile)/split; the run-time engine's tile holds min(8192/n, 512) rows, a
+ * compiled schedule's its own), 0 if n is not in this plan. */
 int gbfft_ragged_tile_split(gbfft_plan p, int64_t n);
+
+/*
+ * Engine of a length in a ragged plan.  Lengths n = p * 2^k (p = 1, 3, 5, 7,
+ * 8 <= n <= 8192) have a compiled schedule inside the persistent kernel (the
+ * single-pass stage engine with the schedule and the tile fixed at compile
+ * time; the default for those lengths); every length can also run the
+ * run-time engine, which reads its radix schedule from the length's
+ * descriptor.  gbfft_ragged_set_engine switches length n (n = 0: every length
+ * of the plan; lengths without a compiled schedule then keep the run-time
+ * engine) to the compiled (1) or run-time (0) engine and rebuilds the queue;
+ * NOT_FOUND if n is not in the plan or has no compiled schedule (compiled =
+ * 1), INVALID_ARG for other values.  gbfft_ragged_engine returns 1 / 0 for
+ * length n, -1 if n is not in the plan or p is not a ragged plan.  The
+ * autotuner may switch either way.
+ */
+gbfft_status gbfft_ragged_set_engine(gbfft_plan p, int64_t n, int compiled);
+int gbfft_ragged_engine(gbfft_plan p, int64_t n);
 
 /*
  * Failure injection and its bound (host side; never faults the GPU): mark

@@ -839,6 +839,16 @@ int gbfft_ragged_schedule(gbfft_plan p, int64_t n, int* radices) {
     return ns;
 }
 
+gbfft_status gbfft_ragged_set_engine(gbfft_plan p, int64_t n, int compiled) {
+    if (!p || p->kind != kPlanRagged || n < 0 || (compiled != 0 && compiled != 1)) return GBFFT_ERR_INVALID_ARG;
+    return ragged_set_engine(p->ragged, n, compiled);
+}
+
+int gbfft_ragged_engine(gbfft_plan p, int64_t n) {
+    if (!p || p->kind != kPlanRagged) return -1;
+    return ragged_engine(p->ragged, n);
+}
+
 int gbfft_ragged_tile_split(gbfft_plan p, int64_t n) {
     if (!p || p->kind != kPlanRagged) return 0;
     return ragged_class_split(p->ragged, n);

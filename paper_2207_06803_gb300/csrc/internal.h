@@ -123,6 +123,8 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
                              float* best_ms);
 int ragged_class_split(const RaggedState* r, int64_t n);
 int ragged_queue_order(const RaggedState* r);
+gbfft_status ragged_set_engine(RaggedState* r, int64_t n, int compiled);
+int ragged_engine(const RaggedState* r, int64_t n);
 // Radix schedule the plan uses for length n (stage count; 0 if n is absent).
 int ragged_schedule(const RaggedState* r, int64_t n, int* radix);
 bool ragged_supported(int64_t n);

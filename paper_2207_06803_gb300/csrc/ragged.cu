@@ -69,8 +69,11 @@ struct RaggedLenState {
     std::vector<int64_t> members;               // transform indices of this length
     std::vector<std::vector<int>> cands;        // candidate schedules
     std::vector<int> tw_base;                   // twiddle-table offset of each candidate
-    int cand = 0;                               // schedule in use
-    int split = 1;                              // tile shape: rows per item = (8192 / n) / split
+    int cand = 0;                               // schedule in use by the run-time engine
+    int split = 1;                              // tile shape: rows per item = (rows of the tile) / split
+    int body = -1;                              // compiled schedule of this length (-1: none)
+    int body_cand = -1;                         // its index in cands (for its twiddle blocks)
+    int use_body = 0;                           // 1: items run the compiled schedule
 };
 
 struct RaggedState {
@@ -115,7 +118,8 @@ void ragged_destroy(RaggedState* r) {
 }
 
 static int rows_per_item(const RaggedLenState& L) {
-    const int64_t rows = (int64_t)kRaggedTile / L.n / L.split;
+    const int64_t tile_rows = L.use_body ? (int64_t)kRaggedBodies[L.body].rows : (int64_t)kRaggedTile / L.n;
+    const int64_t rows = tile_rows / L.split;
     return (int)std::max<int64_t>(1, std::min<int64_t>(kRaggedMaxRows, rows));
 }
 
@@ -126,6 +130,8 @@ static RaggedLen describe(const RaggedLenState& L) {
     d.n = (int)L.n;
     d.nstages = (int)sch.size();
     d.mag_n = ragged_magic((int)L.n);
+    d.body = L.use_body ? L.body : -1;
+    d.tw0 = L.body_cand >= 0 ? L.tw_base[L.body_cand] : 0;
     int l = 1, tw = L.tw_base[L.cand];
     for (int s = 0; s < d.nstages; ++s) {
         RaggedStage& st = d.st[s];
@@ -279,6 +285,16 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
         RaggedLenState& L = r->lens[c];
         L.n = distinct[c];
         L.cands = schedules_of(L.n);
+        L.body = L.n <= kRaggedMaxN ? ragged_body_id((int)L.n) : -1;
+        if (L.body >= 0) {  // the compiled schedule's twiddle blocks come with the candidates
+            std::vector<int> sch;
+            for (int r : kRaggedBodies[L.body].radix)
+                if (r > 0) sch.push_back(r);
+            auto it = std::find(L.cands.begin(), L.cands.end(), sch);
+            if (it == L.cands.end()) it = L.cands.insert(L.cands.end(), sch);
+            L.body_cand = (int)(it - L.cands.begin());
+            L.use_body = 1;
+        }
         for (const auto& sch : L.cands) {
             L.tw_base.push_back(tw_total);
             tw_total += stage_twiddle_count(sch.data(), (int)sch.size());
@@ -454,9 +470,12 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
     });
     for (int c : order) {
         RaggedLenState& L = r->lens[c];
+        if (L.body >= 0) trial(&L.use_body, 1 - L.use_body);
+        const int64_t tile_rows = L.use_body ? (int64_t)kRaggedBodies[L.body].rows : (int64_t)kRaggedTile / L.n;
         for (int sp : {1, 2, 4, 8})
-            if ((int64_t)kRaggedTile / L.n / sp >= 1) trial(&L.split, sp);
-        for (int k = 0; k < (int)L.cands.size(); ++k) trial(&L.cand, k);
+            if (tile_rows / sp >= 1) trial(&L.split, sp);
+        if (!L.use_body)
+            for (int k = 0; k < (int)L.cands.size(); ++k) trial(&L.cand, k);
     }
     if (st == GBFFT_OK) st = ragged_build_items(r);
     ragged_release_graph(r);
@@ -469,6 +488,28 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
 }
 
 int ragged_queue_order(const RaggedState* r) { return r->order; }
+
+gbfft_status ragged_set_engine(RaggedState* r, int64_t n, int compiled) {
+    bool found = false;
+    for (RaggedLenState& L : r->lens) {
+        if (n != 0 && L.n != n) continue;
+        found = true;
+        if (compiled && L.body < 0) {
+            if (n != 0) return GBFFT_ERR_NOT_FOUND;
+            continue;  // n == 0: lengths without a compiled schedule keep the run-time engine
+        }
+        L.use_body = compiled ? 1 : 0;
+    }
+    if (!found) return GBFFT_ERR_NOT_FOUND;
+    ragged_release_graph(r);
+    return ragged_build_items(r);
+}
+
+int ragged_engine(const RaggedState* r, int64_t n) {
+    for (const RaggedLenState& L : r->lens)
+        if (L.n == n) return L.use_body;
+    return -1;
+}
 
 static const RaggedLenState* len_state(const RaggedState* r, int64_t n) {
     for (const RaggedLenState& L : r->lens)
@@ -484,7 +525,7 @@ int ragged_class_split(const RaggedState* r, int64_t n) {
 int ragged_schedule(const RaggedState* r, int64_t n, int* radix) {
     const RaggedLenState* L = len_state(r, n);
     if (!L) return 0;
-    const std::vector<int>& sch = L->cands[L->cand];
+    const std::vector<int>& sch = L->cands[L->use_body ? L->body_cand : L->cand];
     for (size_t i = 0; i < sch.size(); ++i) radix[i] = sch[i];
     return (int)sch.size();
 }

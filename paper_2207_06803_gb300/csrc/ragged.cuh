@@ -5,15 +5,18 @@
 // 16), cuts each group into work items of at most T rows (T * n <= 8192
 // complex elements), orders the items and uploads them with the list of row
 // offsets and one descriptor per length.  Each CTA of the persistent kernel
-// repeatedly claims the next item with one atomic increment and runs the
-// item's schedule stage by stage: the first stage reads the rows straight from
-// HBM, stages exchange through a shared-memory tile, the last stage writes
-// straight to HBM (the stage algebra of the single-pass kernel, Eq. 2, with
-// the schedule read at run time instead of compiled per length).  Because
-// only the radix is compiled (one code path per radix and stage position), a
-// single kernel serves every length n <= 8192 whose prime factors are 2, 3, 5
-// and 7, with a small instruction footprint and without the register pressure
-// of per-length fully unrolled schedules.
+// repeatedly claims queue items (in chunks of consecutive items, one atomic
+// per chunk) and runs each item's schedule: the first stage reads the rows
+// straight from HBM, stages exchange through a shared-memory tile, the last
+// stage writes straight to HBM (the stage algebra of the single-pass kernel,
+// Eq. 2).  Two engines run a schedule:
+//   compiled  for n = p * 2^k (p = 1, 3, 5, 7, 8 <= n <= 8192): the schedule
+//             and the tile are fixed at compile time, one non-inlined function
+//             per length with its own register allocation (constant strides
+//             fold into addressing: a third fewer instructions than the
+//             run-time engine on the 41-length mix);
+//   run-time  any n <= 8192 whose prime factors are 2, 3, 5, 7: the schedule is
+//             read from the length's descriptor, one code path per radix.
 //
 // Items carry a `ready` word.  The host publishes all items ready; a CTA that
 // claims an item still marked not ready waits for it with a bounded spin
@@ -58,9 +61,81 @@ struct RaggedStage {
 struct RaggedLen {
     int n, nstages;
     unsigned mag_n;
-    int pad;
+    int body;  // compiled schedule (index into the body list below), or -1: the run-time stage engine
+    int tw0;   // offset of the compiled schedule's stage-twiddle blocks in the plan's table
+    int pad[3];
     RaggedStage st[kRaggedMaxStages];
 };
+static_assert(sizeof(RaggedLen) % 16 == 0, "descriptors are copied in 16-byte pieces");
+constexpr int kRaggedLenChunks = (int)(sizeof(RaggedLen) / 16);
+static_assert(sizeof(RaggedItem) == 16, "queue entries are copied in one 16-byte piece");
+
+// Compiled schedules.  For the lengths n = p * 2^k (p = 1, 3, 5, 7, 8 <= n <=
+// 8192) an item runs a schedule fixed at compile time: the single-pass stage
+// engine of stockham.cuh with constant strides, so index arithmetic folds into
+// addressing and the twiddle loop bounds are known.  X(N, T, radices...): T
+// rows per item (T * N <= 8192 elements; for p = 3, 5, 7 the tile is capped so
+// that the radix-p stage holds at most 16 complex per thread), radices in
+// application order (the odd radix first, as in the single-pass variants).
+// Every other 7-smooth length runs the run-time engine.
+#define GBFFT_RAGGED_BODIES(X)   \
+    X(8, 512, 2, 4)              \
+    X(16, 512, 4, 4)             \
+    X(32, 256, 4, 8)             \
+    X(64, 128, 4, 16)            \
+    X(128, 64, 8, 16)            \
+    X(256, 32, 16, 16)           \
+    X(512, 16, 2, 16, 16)        \
+    X(1024, 8, 4, 16, 16)        \
+    X(2048, 4, 16, 16, 8)        \
+    X(4096, 2, 16, 16, 16)       \
+    X(8192, 1, 16, 16, 16, 2)    \
+    X(12, 512, 3, 4)             \
+    X(24, 320, 3, 8)             \
+    X(48, 160, 3, 16)            \
+    X(96, 80, 3, 2, 16)          \
+    X(192, 40, 3, 4, 16)         \
+    X(384, 20, 3, 8, 16)         \
+    X(768, 10, 3, 16, 16)        \
+    X(1536, 5, 3, 16, 16, 2)     \
+    X(3072, 2, 3, 16, 16, 4)     \
+    X(6144, 1, 3, 16, 16, 8)     \
+    X(10, 512, 5, 2)             \
+    X(20, 384, 5, 4)             \
+    X(40, 192, 5, 8)             \
+    X(80, 96, 5, 16)             \
+    X(160, 48, 5, 2, 16)         \
+    X(320, 24, 5, 4, 16)         \
+    X(640, 12, 5, 8, 16)         \
+    X(1280, 6, 5, 16, 16)        \
+    X(2560, 3, 5, 16, 16, 2)     \
+    X(5120, 1, 5, 16, 16, 4)     \
+    X(14, 512, 7, 2)             \
+    X(28, 256, 7, 4)             \
+    X(56, 128, 7, 8)             \
+    X(112, 64, 7, 16)            \
+    X(224, 32, 7, 2, 16)         \
+    X(448, 16, 7, 4, 16)         \
+    X(896, 8, 7, 8, 16)          \
+    X(1792, 4, 7, 16, 16)        \
+    X(3584, 2, 7, 16, 16, 2)     \
+    X(7168, 1, 7, 16, 16, 4)
+
+// Host-side description of a compiled schedule (plan building, autotuner).
+struct RaggedBodyInfo {
+    int n, rows;
+    int radix[kRaggedMaxStages];
+};
+#define GBFFT_RAGGED_BODY_INFO(N, T, ...) {N, T, {__VA_ARGS__}},
+constexpr RaggedBodyInfo kRaggedBodies[] = {GBFFT_RAGGED_BODIES(GBFFT_RAGGED_BODY_INFO)};
+#undef GBFFT_RAGGED_BODY_INFO
+constexpr int kRaggedNumBodies = (int)(sizeof(kRaggedBodies) / sizeof(kRaggedBodies[0]));
+
+constexpr int ragged_body_id(int n) {
+    for (int i = 0; i < kRaggedNumBodies; ++i)
+        if (kRaggedBodies[i].n == n) return i;
+    return -1;
+}
 
 // Division by an invariant integer with a multiply-high (the method of
 // Granlund and Montgomery, 1994): with m = ceil(2^31 / d),
@@ -173,6 +248,70 @@ __device__ __forceinline__ void ragged_stage(bool src_smem, bool dst_smem, const
     }
 }
 
+// Rows of an item: row t starts at complex element off[t] of both buffers
+// (the offsets stay in global memory, read once per butterfly through the
+// read-only path).
+struct RaggedIO {
+    const float2* in;
+    float2* out;
+    const long long* __restrict__ off;
+    __device__ __forceinline__ float2 ld(int t, int n) const { return in[off[t] + n]; }
+    __device__ __forceinline__ void st(int t, int n, float2 v) const { out[off[t] + n] = v; }
+};
+
+// One item on a compiled schedule: stage 1 reads the rows from HBM, stages
+// exchange through the padded tile, the last stage writes HBM; rows t >=
+// nvalid of the T-row tile are skipped.  The caller has synchronised since
+// the tile's last readers.
+template <int N, int S, int T, int... Rs>
+__device__ __noinline__ void ragged_body(const float2* in, float2* out, const long long* __restrict__ off, float2* sm,
+                                         const float2* __restrict__ tw, int nvalid) {
+    constexpr int E = capacity_of_r<N, T, kRaggedThreads, Rs...>();
+    static_assert(T * N <= kRaggedTile && E <= 16, "compiled ragged tile too large");
+    float2 v[E];
+    const RaggedIO io{in, out, off};
+    gather_global<N, E, T, First<Rs...>::value, RaggedIO, kRaggedThreads>(v, io, nvalid);
+    run_stages_t<N, S, E, T, 4, kRaggedThreads, false, 0, 1, Rs...>(v, io, sm, tw, nvalid);
+}
+
+template <int S>
+__device__ __forceinline__ void ragged_compiled(int body, const float2* in, float2* out, const long long* off,
+                                                float2* sm, const float2* __restrict__ tw, int nvalid) {
+    switch (body) {
+#define GBFFT_RAGGED_BODY_CASE(N, T, ...)                          \
+    case ragged_body_id(N):                                        \
+        ragged_body<N, S, T, __VA_ARGS__>(in, out, off, sm, tw, nvalid);     \
+        break;
+        GBFFT_RAGGED_BODIES(GBFFT_RAGGED_BODY_CASE)
+#undef GBFFT_RAGGED_BODY_CASE
+        default:
+            break;
+    }
+}
+
+// Asynchronous global -> shared copies (cp.async): complete per thread at
+// ragged_cp_async_wait, visible to the CTA after the next barrier.
+__device__ __forceinline__ void ragged_cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void ragged_cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void ragged_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Queue entries are claimed by thread 0 in chunks of kRaggedChunk consecutive
+// entries (one atomic per chunk, issued a chunk ahead).  Consecutive entries
+// mostly share a length, so a CTA tends to run the same compiled schedule
+// several times in a row (its instructions stay cached).
+constexpr int kRaggedChunk = 2;
+
+// The persistent kernel.  The queue's latencies are taken off the path between
+// items: during item i, thread 0 claims the entry of item i+2 and copies it
+// into shared memory (cp.async), and every thread copies the length descriptor
+// and row offsets of item i+1 into the other descriptor slot (cp.async).  One
+// barrier opens each item.  An item then runs its compiled schedule (the
+// single-pass stage engine with the schedule fixed at compile time) or the
+// run-time engine (the schedule read from its descriptor, one stage at a time).
 template <int S>
 __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, float2* out, const RaggedItem* items,
                                                            int nitems, const long long* offs,
@@ -180,75 +319,107 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
                                                            const float2* __restrict__ tw, int* counter, int* status,
                                                            long long wait_ns) {
     extern __shared__ float2 sm[];
-    __shared__ long long s_off[kRaggedMaxRows];
-    __shared__ RaggedLen s_len;
-    __shared__ int s_item, s_ok;
-    int next = 0;  // thread 0: the item claimed for the next round
-    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
-    for (;;) {
-        __syncthreads();  // the previous item's readers of s_off, s_len and sm are done
-        if (threadIdx.x == 0) {
-            const int it = next;
+    __shared__ __align__(16) long long s_off[2][kRaggedMaxRows];
+    __shared__ __align__(16) RaggedLen s_len[2];
+    __shared__ __align__(16) RaggedItem s_item[3];
+    __shared__ int s_id[3];
+    __shared__ int s_ok;
+    const int tid = threadIdx.x;
+    // Descriptor and row offsets of queue entry d into descriptor slot ls (every thread).
+    auto fetch = [&](const RaggedItem& d, int ls) {
+        if (tid < kRaggedLenChunks)
+            ragged_cp_async16(reinterpret_cast<char*>(&s_len[ls]) + 16 * tid,
+                              reinterpret_cast<const char*>(lens + d.cls) + 16 * tid);
+        for (int t = tid; t < d.count; t += kRaggedThreads) ragged_cp_async8(&s_off[ls][t], offs + d.first + t);
+    };
+    int c_pos = 0, c_end = 0, n_pos = 0;  // thread 0: current chunk [c_pos, c_end), start of the next
+    auto claim = [&]() {                   // thread 0: the next queue index
+        const int it = c_pos;
+        if (it < nitems && ++c_pos == c_end) {
+            c_pos = n_pos;
+            c_end = n_pos + kRaggedChunk;
+            n_pos = atomicAdd(counter, kRaggedChunk);
+        }
+        return it;
+    };
+    if (tid == 0) {
+        c_pos = atomicAdd(counter, kRaggedChunk);
+        c_end = c_pos + kRaggedChunk;
+        n_pos = atomicAdd(counter, kRaggedChunk);
+        for (int k = 0; k < 2; ++k) {
+            const int id = claim();
+            s_id[k] = id;
+            if (id < nitems) ragged_cp_async16(&s_item[k], items + id);
+        }
+        ragged_cp_async_wait();
+    }
+    __syncthreads();
+    if (s_id[0] < nitems) fetch(s_item[0], 0);
+    for (int i = 0;; ++i) {
+        const int cur = i % 3, nxt = (i + 1) % 3, aft = (i + 2) % 3, ls = i & 1;
+        if (tid == 0) {  // this item's entry was read an item ago; wait (bounded) if it was not ready then
             int ok = 1;
-            if (it < nitems) {
-                next = atomicAdd(counter, 1);  // claimed now, used next round: the latency overlaps this item
+            const int it = s_id[cur];
+            if (it < nitems && s_item[cur].ready == 0) {
                 const volatile int* rdy = &items[it].ready;
-                if (*rdy == 0) {
-                    const unsigned long long t0 = globaltimer_ns();
-                    while (*rdy == 0) {
-                        if (globaltimer_ns() - t0 > (unsigned long long)wait_ns) {
-                            ok = 0;
-                            atomicCAS(status, 0, (int)GBFFT_ERR_TIMEOUT);
-                            break;
-                        }
-                        __nanosleep(2000);
+                const unsigned long long t0 = globaltimer_ns();
+                while (*rdy == 0) {
+                    if (globaltimer_ns() - t0 > (unsigned long long)wait_ns) {
+                        ok = 0;
+                        atomicCAS(status, 0, (int)GBFFT_ERR_TIMEOUT);
+                        break;
                     }
+                    __nanosleep(2000);
                 }
             }
-            s_item = it;
             s_ok = ok;
         }
-        __syncthreads();
-        const int it = s_item;
+        ragged_cp_async_wait();  // this thread's copies of the item's descriptor and offsets
+        __syncthreads();         // the previous item's readers of the tile and of the other slot are done
+        const int it = s_id[cur];
         if (it >= nitems) break;
-        if (!s_ok) continue;
-        const RaggedItem d = items[it];
-        for (int t = threadIdx.x; t < d.count; t += kRaggedThreads) s_off[t] = offs[d.first + t];
-        {
-            const int* src = reinterpret_cast<const int*>(lens + d.cls);
-            int* dst = reinterpret_cast<int*>(&s_len);
-            for (int w = threadIdx.x; w < (int)(sizeof(RaggedLen) / sizeof(int)); w += kRaggedThreads)
-                dst[w] = __ldg(src + w);
+        const int count = s_item[cur].count;
+        if (s_id[nxt] < nitems) fetch(s_item[nxt], ls ^ 1);
+        if (tid == 0) {
+            const int id = claim();
+            s_id[aft] = id;
+            if (id < nitems) ragged_cp_async16(&s_item[aft], items + id);
         }
-        __syncthreads();
-        const int n = s_len.n, ns = s_len.nstages;
+        if (!s_ok) continue;
+        const long long* off = s_off[ls];
+        const int body = s_len[ls].body;
+        if (body >= 0) {
+            ragged_compiled<S>(body, in, out, off, sm, tw + s_len[ls].tw0, count);
+            continue;
+        }
+        const int n = s_len[ls].n, ns = s_len[ls].nstages;
         if (ns == 0) {  // n == 1: DFT_1 is the identity
-            for (int t = threadIdx.x; t < d.count; t += kRaggedThreads) out[s_off[t]] = in[s_off[t]];
+            for (int t = tid; t < count; t += kRaggedThreads) out[off[t]] = in[off[t]];
             continue;
         }
         // A one-stage schedule (n <= 16) also goes through the tile, then a
         // copy writes the rows out, so that no stage reads and writes HBM.
         for (int s = 0; s < ns; ++s) {
-            const RaggedStage st = s_len.st[s];
+            const RaggedStage st = s_len[ls].st[s];
             const bool src_smem = s > 0, dst_smem = s < ns - 1 || ns == 1;
             switch (st.r) {
-                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
-                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
-                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
-                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
-                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
-                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
-                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, out, s_off, sm, tw, st, n, d.count); break;
+                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
                 default:
-                    if (threadIdx.x == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
+                    if (tid == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
                     break;
             }
         }
         if (ns == 1) {
-            const unsigned mag_n = s_len.mag_n;
-            for (int idx = threadIdx.x; idx < d.count * n; idx += kRaggedThreads) {
+            const unsigned mag_n = s_len[ls].mag_n;
+            for (int idx = tid; idx < count * n; idx += kRaggedThreads) {
                 const int t = rdiv(idx, mag_n), j = idx - t * n;
-                out[s_off[t] + j] = sm[rpad(idx)];
+                out[off[t] + j] = sm[rpad(idx)];
             }
         }
     }

@@ -80,6 +80,8 @@ PROTOTYPES = {
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
     "gbfft_ragged_queue_order": (_c_int, [_c_vp]),
     "gbfft_ragged_schedule": (_c_int, [_c_vp, _c_i64, _c_intp]),
+    "gbfft_ragged_set_engine": (_c_int, [_c_vp, _c_i64, _c_int]),
+    "gbfft_ragged_engine": (_c_int, [_c_vp, _c_i64]),
     "gbfft_plan_create_nd": (_c_int, [ctypes.POINTER(_c_vp), _c_int, _c_i64p, _c_i64, _c_int, _c_int]),
     "gbfft_plan_dims": (_c_int, [_c_vp, _c_intp, _c_i64p]),
     "gbfft_server_timing": (_c_int, [_c_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
@@ -359,6 +361,14 @@ def gbfft_ragged_schedule(plan: int, n: int) -> list[int]:
     rad = (ctypes.c_int * 8)()
     ns = int(lib().gbfft_ragged_schedule(plan, n, rad))
     return list(rad[:max(ns, 0)])
+
+
+def gbfft_ragged_set_engine(plan: int, n: int, compiled: int) -> None:
+    _check(lib().gbfft_ragged_set_engine(plan, n, compiled), "gbfft_ragged_set_engine")
+
+
+def gbfft_ragged_engine(plan: int, n: int) -> int:
+    return int(lib().gbfft_ragged_engine(plan, n))
 
 
 def gbfft_ragged_queue_order(plan: int) -> int:

@@ -51,12 +51,20 @@ def to_np(t):
     return t.cpu().numpy().view(np.complex64)
 
 
+@pytest.mark.parametrize("engine", ["compiled", "runtime"])
 @pytest.mark.parametrize("direction", [-1, 1])
-def test_ragged_10000_transforms_41_sizes(direction):
+def test_ragged_10000_transforms_41_sizes(direction, engine):
+    """Every one of the 41 family lengths has a compiled schedule (the
+    default); the same plan switched to the run-time engine must agree with the
+    oracle too."""
     from paper_2207_06803_gb300 import gbfft
     sizes, offs, flat = ragged_case(10000)
     assert len(set(sizes.tolist())) == 41
     with gbfft.RaggedPlan(sizes, offs, direction) as p:
+        assert all(gbfft.gbfft_ragged_engine(p.handle, n) == 1 for n in set(sizes.tolist()))
+        if engine == "runtime":
+            gbfft.gbfft_ragged_set_engine(p.handle, 0, 0)
+            assert all(gbfft.gbfft_ragged_engine(p.handle, n) == 0 for n in set(sizes.tolist()))
         assert p.num_items() > 0
         _, d_out = run_plan(p, flat)
         assert gbfft.gbfft_plan_device_status(p.handle) == 0
@@ -185,7 +193,12 @@ def test_ragged_errors():
     with pytest.raises(gbfft.GbfftError) as e:
         gbfft.gbfft_plan_ragged([16], [-1])
     assert e.value.status == gbfft.GBFFT_ERR_INVALID_ARG
-    with gbfft.RaggedPlan([16, 8192], [0, 16]) as p:
+    with gbfft.RaggedPlan([16, 8192, 9], [0, 16, 8208]) as p:
+        assert gbfft.gbfft_ragged_engine(p.handle, 9) == 0      # no compiled schedule for 9
+        assert gbfft.gbfft_ragged_engine(p.handle, 32) == -1    # not in the plan
+        with pytest.raises(gbfft.GbfftError) as e:
+            gbfft.gbfft_ragged_set_engine(p.handle, 9, 1)
+        assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
         with pytest.raises(gbfft.GbfftError):
             gbfft.gbfft_execute(p.handle, 0, 0)
         with pytest.raises(gbfft.GbfftError) as e:
