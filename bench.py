@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
-    ap.add_argument("--config", choices=["sweep", "twopass", "tc", "ragged", "serving", "f64", "nd", "pease"],
+    ap.add_argument("--config", choices=["sweep", "pr1", "twopass", "tc", "ragged", "serving", "f64", "nd", "pease"],
                     default="sweep",
                     help="sweep (default, the headline line) or one of the other configurations")
     ap.add_argument("--seed", type=int, default=None)
@@ -374,7 +374,22 @@ def run_gpu(args):
                 if peak_src == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_launch": BYTES_PER_CALL}
 
-    # Round-trip accuracy (no oracle on this leg): ||inv(fwd(x)) - N x|| / ||N x|| on 256 rows per size.
+    # Accuracy of what was timed, after the timed region: every plan runs once more on the same
+    # input and 256 seeded rows of its output are checked against the FP64 oracle.
+    oracle_acc = {}
+    if rank == 0:
+        for (n, direction), p in plans:
+            batch = TOTAL // n
+            with torch.cuda.stream(stream):
+                p.execute(d_in, d_out, stream)
+            stream.synchronize()
+            rows = synth.sample_rows(seed + n, batch, 256)
+            y = sampled_rows(torch, np, d_out, batch, n, rows)
+            x = flat.reshape(batch, n)[rows]
+            oracle_acc.setdefault(str(n), {})["fwd" if direction < 0 else "inv"] = \
+                accuracy_vs_oracle(y, x, direction, gate(n, FP32_GATE))
+
+    # Round trip as well: ||inv(fwd(x)) - N x|| / ||N x|| on 256 rows per size.
     roundtrip = {}
     with torch.cuda.stream(stream):
         for n in SWEEP:
@@ -421,6 +436,8 @@ def run_gpu(args):
             "clocks": clk,
             "per_size_gbs": per_size,
             "frac_of_hbm_per_size": {k: {kk: vv / peak for kk, vv in v.items()} for k, v in per_size.items()},
+            "oracle_rel_l2": oracle_acc,
+            "oracle_all_pass": all(v["pass"] for d in oracle_acc.values() for v in d.values()),
             "roundtrip_rel_l2_max": roundtrip,
             "gpu": torch.cuda.get_device_name(),
             "other_configs": others,
@@ -439,7 +456,7 @@ def other_configs(args):
     out = {}
     small = argparse.Namespace(**vars(args))
     small.steps = 40
-    for name, fn in (("twopass", run_twopass), ("tc", lambda a: run_tc(a, dists=("uniform",))),
+    for name, fn in (("pr1", run_pr1), ("twopass", run_twopass), ("tc", lambda a: run_tc(a, dists=("uniform",))),
                      ("ragged", run_ragged), ("f64", run_f64), ("nd", run_nd),
                      ("serving", lambda a: run_serving(a, rates=(1000, 10000), scale=0.2, serial_rates=(1000,)))):
         try:
@@ -448,22 +465,30 @@ def other_configs(args):
             out[name] = {"error": f"{type(e).__name__}: {e}"}
             continue
         if name == "twopass":
-            out[name] = {n: {"two_pass_gbs": round(v["alg_gbs"], 1),
-                             **({"cluster_gbs": round(v["cluster_gbs"], 1)} if "cluster_gbs" in v else {})}
+            out[name] = {n: {"two_pass_gbs": round(v["alg_gbs"], 1), "oracle_rel_l2_max": v["oracle"]["rel_l2_max"],
+                             **({"cluster_gbs": round(v["cluster_gbs"], 1),
+                                 "cluster_oracle_rel_l2_max": v["cluster_oracle"]["rel_l2_max"]}
+                                if "cluster_gbs" in v else {})}
                          for n, v in r["per_size"].items()}
         elif name == "tc":
             out[name] = {k: {"gbs": round(v["gbs"], 1), "vs_fp32": round(v["vs_fp32"], 3),
+                             "oracle_rel_l2_max": v["oracle"]["rel_l2_max"], "gate": v["oracle"]["gate"],
                              "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for k, v in r["results"].items()}
         elif name == "nd":
-            out[name] = {k: {"alg_gbs": round(v["alg_gbs"], 1), "frac_actual_of_hbm": round(v["frac_actual_of_hbm"], 3)}
+            out[name] = {k: {"alg_gbs": round(v["alg_gbs"], 1), "frac_actual_of_hbm": round(v["frac_actual_of_hbm"], 3),
+                             "oracle_rel_l2_max": v["oracle"]["rel_l2_max"]}
                          for k, v in r["per_shape"].items()}
         elif name == "f64":
             out[name] = {n: {"fwd_gflops": round(v["fwd"]["gflops"], 1), "fwd_gbs": round(v["fwd"]["gbs"], 1),
+                             "oracle_rel_l2_max": v["oracle"]["rel_l2_max"],
                              "roundtrip_rel_l2_max": v["roundtrip_rel_l2_max"]} for n, v in r["per_size"].items()}
         elif name == "ragged":
             res = r["results"]
             out[name] = {k: res[k] for k in ("ragged_graph_tuned_us", "ragged_gbs", "per_size_us", "per_transform_us",
                                              "speedup_vs_per_size", "speedup_vs_per_transform", "items")}
+            out[name]["oracle_rel_l2_max"] = res["oracle"]["rel_l2_max"]
+        elif name == "pr1":
+            out[name] = {k: r[k] for k in ("us", "gbs", "oracle", "cpu_naive_1core_s", "cpu_naive_all_cores_s")}
         else:
             out[name] = {"batching": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s", "gb_per_s",
                                                                "service_over_10ms")}
@@ -504,6 +529,46 @@ def run_e2e(torch, np, flat, plans, stream, world, e2e_steps, calls):
 # Other configurations (one JSON line each; not the headline line)
 # --------------------------------------------------------------------------
 
+# --------------------------------------------------------------------------
+# Accuracy of timed outputs against the FP64 oracle (always outside the timed
+# regions: the outputs are copied back after timing, sampled rows only)
+# --------------------------------------------------------------------------
+
+FP32_GATE, TC_GATE, F64_GATE = 2e-7, 1e-6, 1e-15  # rel-L2 per log2(N)
+
+
+def gate(n: int, per_log2: float) -> float:
+    return per_log2 * max(1.0, math.log2(n))
+
+
+def accuracy_vs_oracle(y, x, sign: int, tol: float, naive: bool = False) -> dict:
+    """Per-row relative L2 error ||y - ref|| / ||ref|| of rows `y` (the device
+    output, complex) against the FP64 oracle on the same input rows `x`, with
+    max / mean / p99, the paper's form max|y - ref| / N (Sec. VI) and the gate."""
+    import numpy as np
+
+    import oracle
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    fn = oracle.dft_naive if naive else oracle.dft
+    ref = fn(x, sign, nthreads=os.cpu_count() or 1)
+    y = np.asarray(y, dtype=np.complex128).reshape(ref.shape)
+    num = np.linalg.norm(y - ref, axis=1)
+    den = np.linalg.norm(ref, axis=1)
+    err = np.where(den > 0, num / np.where(den > 0, den, 1.0), num)
+    return {"rows": int(err.size), "rel_l2_max": float(err.max()), "rel_l2_mean": float(err.mean()),
+            "rel_l2_p99": float(np.percentile(err, 99)), "max_abs_over_n": float(np.abs(y - ref).max() / x.shape[1]),
+            "gate": tol, "pass": bool(err.max() <= tol)}
+
+
+def sampled_rows(torch, np, d_out, batch: int, n: int, rows, complex_dtype=None):
+    """Rows `rows` of a (batch, n) complex buffer on the device, copied to the host."""
+    complex_dtype = complex_dtype or np.complex64
+    floats_per_row = 2 * n
+    idx = torch.from_numpy(np.asarray(rows, dtype=np.int64)).to(d_out.device)
+    sel = d_out[: batch * floats_per_row].view(batch, floats_per_row).index_select(0, idx)
+    return sel.cpu().numpy().view(complex_dtype)
+
+
 def _time_ms(torch, fn, reps, stream):
     """Median CUDA-event time of fn() over reps runs on `stream` (after 3 warm-ups)."""
     for _ in range(3):
@@ -525,6 +590,45 @@ def _peak():
     return float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)), src
 
 
+def run_pr1(args):
+    """The small reference case: forward c2c N = 64, batch 4096, complex64 rows uniform[-1, 1) from the
+    default seed, every row checked against the oracle's direct DFT (the definition, Sec. II).  The
+    2 MiB input stays in L2, so the GB/s (16 B per point) is not an HBM figure; the direct DFT on the
+    host is timed on one core (the paper's single-thread setting) and on all cores."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n, batch = 64, 4096
+    seed = synth.DEFAULT_SEED if args.seed is None else args.seed
+    flat = synth.uniform_flat(seed, 0, n * batch)
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    d_out = torch.empty_like(d_in)
+    with gbfft.Plan(n, batch, -1) as p:
+        ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(100, args.steps), stream)
+        torch.cuda.synchronize()
+        assert gbfft.gbfft_plan_device_status(p.handle) == 0
+        info = p.info()
+    y = d_out.cpu().numpy().view(np.complex64).reshape(batch, n)
+    x = flat.reshape(batch, n)
+    acc = accuracy_vs_oracle(y, x, -1, gate(n, FP32_GATE), naive=True)
+    xd = x.astype(np.complex128)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.dft_naive(xd, -1, nthreads=1)
+    t1 = time.perf_counter()
+    oracle.dft_naive(xd, -1, nthreads=cores)
+    t2 = time.perf_counter()
+    return {"config": "pr1", "metric": "forward c2c N=64 batch=4096: time, GB/s (16 B/point) and error of every row "
+                                       "against the FP64 direct DFT",
+            "n": n, "batch": batch, "seed": seed, "radices": info["radices"], "us": 1e3 * ms,
+            "gbs": 16.0 * n * batch / (ms * 1e-3) / 1e9, "l2_resident": True, "oracle": acc,
+            "cpu_naive_1core_s": t1 - t0, "cpu_naive_all_cores_s": t2 - t1, "cpu_cores": cores}
+
+
 def run_twopass(args):
     """Eq. 2 two-pass lengths 5120..16384 at 2^26 points per call."""
     import numpy as np
@@ -540,9 +644,13 @@ def run_twopass(args):
     for n in (5120, 6144, 7168, 8192, 10240, 12288, 14336, 16384, 20480, 24576, 28672, 32768, 65536):
         batch = TOTAL // n
         res = {}
+        rows_chk = synth.sample_rows(synth.DEFAULT_SEED + n, batch, 64)
+        x_chk = flat.reshape(-1)[: batch * n].reshape(batch, n)[rows_chk]
         with gbfft.Plan(n, batch, -1, k_outer=0) as p:  # Eq. 2 as two passes (two HBM round trips): the default
             info = p.info()
             ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+        res["oracle"] = accuracy_vs_oracle(sampled_rows(torch, np, d_out, batch, n, rows_chk), x_chk, -1,
+                                           gate(n, FP32_GATE))
         alg = 16.0 * n * batch / (ms * 1e-3) / 1e9
         res.update({"k_outer": info["k_outer"], "m_inner": info["m_inner"], "ms": ms, "alg_gbs": alg,
                     "actual_gbs_two_round_trips": 2 * alg, "frac_actual_of_hbm": 2 * alg / peak})
@@ -550,6 +658,8 @@ def run_twopass(args):
             with gbfft.Plan(n, batch, -1, variant=0) as p:
                 rad = p.info()["radices"]
                 ms1 = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+            res["cluster_oracle"] = accuracy_vs_oracle(sampled_rows(torch, np, d_out, batch, n, rows_chk), x_chk, -1,
+                                                       gate(n, FP32_GATE))
             alg1 = 16.0 * n * batch / (ms1 * 1e-3) / 1e9
             res.update({"cluster_radices": rad, "cluster_ms": ms1, "cluster_gbs": alg1,
                         "cluster_frac_of_hbm": alg1 / peak, "cluster_vs_two_pass": ms / ms1})
@@ -581,7 +691,17 @@ def run_nd(args):
         with gbfft.Plan(dims, batch, -1) as p:
             ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
         alg = 16.0 * total * batch / (ms * 1e-3) / 1e9
-        rows["x".join(map(str, dims))] = {"batch": batch, "ms": ms, "alg_gbs": alg,
+        items = synth.sample_rows(synth.DEFAULT_SEED + total, batch, 4)
+        y = sampled_rows(torch, np, d_out, batch, total, items)
+        x = flat[: batch * total].reshape(batch, total)[items]
+        import oracle
+        ref = oracle.dft_nd(x.astype(np.complex128).reshape((-1,) + tuple(dims)), -1,
+                            nthreads=os.cpu_count() or 1).reshape(len(items), total)
+        err = np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        acc = {"items": int(len(items)), "rel_l2_max": float(err.max()), "rel_l2_mean": float(err.mean()),
+               "max_abs_over_n": float(np.abs(y - ref).max() / total), "gate": gate(total, FP32_GATE),
+               "pass": bool(err.max() <= gate(total, FP32_GATE))}
+        rows["x".join(map(str, dims))] = {"batch": batch, "ms": ms, "alg_gbs": alg, "oracle": acc,
                                           "actual_gbs": alg * len(dims), "frac_actual_of_hbm": alg * len(dims) / peak}
     return {"config": "nd", "metric": "multi-dimensional c2c GB/s (16 B/point algorithmic; one HBM round trip per axis)",
             "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_shape": rows}
@@ -590,8 +710,7 @@ def run_nd(args):
 def run_pease(args):
     """Pease's constant-geometry factorisation (variant kind 5) against the default Stockham plan on
     the same lengths: N = 64, 256, 512, 4096 at 2^26 points per call, forward; GB/s on 16 B/point
-    and the relative L2 error of sampled rows against numpy.fft in complex128 (a spot check;
-    the parity tests compare with the oracle)."""
+    and the relative L2 error of 256 sampled rows against the FP64 oracle."""
     import numpy as np
     import torch
     from paper_2207_06803_gb300 import gbfft, synth
@@ -610,13 +729,12 @@ def run_pease(args):
             with gbfft.Plan(n, batch, -1, variant=variant) as p:
                 ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
                 torch.cuda.synchronize()
-            sample = synth.sample_rows(synth.DEFAULT_SEED, batch, 16)
-            y = d_out.view(batch, 2 * n)[torch.from_numpy(sample).cuda()].cpu().numpy().view(np.complex64)
-            x = flat.reshape(batch, n)[sample].astype(np.complex128)
-            ref = np.fft.fft(x, axis=1)
-            err = float((np.linalg.norm(y - ref, axis=1) / np.linalg.norm(ref, axis=1)).max())
+            sample = synth.sample_rows(synth.DEFAULT_SEED + n, batch, 256)
+            y = sampled_rows(torch, np, d_out, batch, n, sample)
+            x = flat.reshape(batch, n)[sample]
             gbs = 16.0 * n * batch / (ms * 1e-3) / 1e9
-            res[name] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "rel_l2_max_vs_numpy_fft": err}
+            res[name] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak,
+                         "oracle": accuracy_vs_oracle(y, x, -1, gate(n, FP32_GATE))}
         res["pease_vs_stockham"] = res["pease"]["gbs"] / res["stockham_default"]["gbs"]
         rows[str(n)] = res
     return {"config": "pease", "metric": "Pease constant-geometry vs Stockham c2c GB/s (16 B/point)",
@@ -660,6 +778,9 @@ def run_f64(args):
             pf.execute(d_in, d_out, stream)
             pi.execute(d_out, d_rt, stream)
         torch.cuda.synchronize()
+        rows_chk = synth.sample_rows(synth.DEFAULT_SEED + n, batch, 256)
+        res["oracle"] = accuracy_vs_oracle(sampled_rows(torch, np, d_out, batch, n, rows_chk, np.complex128),
+                                           flat[: batch * n].reshape(batch, n)[rows_chk], -1, gate(n, F64_GATE))
         sample = torch.from_numpy(synth.sample_rows(synth.DEFAULT_SEED, batch, 256)).cuda()
         a = d_rt[: 2 * n * batch].view(batch, 2 * n).index_select(0, sample).cpu().numpy().view(np.complex128)
         b = d_in[: 2 * n * batch].view(batch, 2 * n).index_select(0, sample).cpu().numpy().view(np.complex128) * n
@@ -698,7 +819,10 @@ def run_tc(args, dists=("uniform", "gaussian_scaled")):
             rr = d_rt.view(batch, 2 * n)[:4096].double()
             rt = (torch.linalg.vector_norm(rr - n * xr, dim=1) / torch.linalg.vector_norm(n * xr, dim=1)).max()
             gbs = BYTES_PER_CALL / (ms * 1e-3) / 1e9
-            out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak,
+            rows_chk = synth.sample_rows(synth.DEFAULT_SEED + n, batch, 256)
+            acc = accuracy_vs_oracle(sampled_rows(torch, np, d_out, batch, n, rows_chk),
+                                     x.reshape(batch, n)[rows_chk], -1, gate(n, FP32_GATE if dt == 0 else TC_GATE))
+            out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "oracle": acc,
                                          "roundtrip_rel_l2_max": float(rt)}
     # the direct DFT (one split-FP16 matrix product per 128 transforms) for small N
     direct_sizes = [int(v) for v in args.sizes.split(",")] if getattr(args, "sizes", None) else \
@@ -719,13 +843,35 @@ def run_tc(args, dists=("uniform", "gaussian_scaled")):
             rr = d_rt.view(batch, 2 * n)[:4096].double()
             rt = (torch.linalg.vector_norm(rr - n * xr, dim=1) / torch.linalg.vector_norm(n * xr, dim=1)).max()
             gbs = 16.0 * n * batch / (ms * 1e-3) / 1e9
-            out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak,
+            rows_chk = synth.sample_rows(synth.DEFAULT_SEED + n, batch, 256)
+            acc = accuracy_vs_oracle(sampled_rows(torch, np, d_out, batch, n, rows_chk),
+                                     x[: batch * n].reshape(batch, n)[rows_chk], -1,
+                                     gate(n, FP32_GATE if dt == 0 else TC_GATE))
+            out[f"{n}/{dist}/{name}"] = {"ms": ms, "gbs": gbs, "frac_of_hbm": gbs / peak, "oracle": acc,
                                          "roundtrip_rel_l2_max": float(rt)}
     for key in list(out):
         n, dist, name = key.split("/")
         out[key]["vs_fp32"] = out[key]["gbs"] / out[f"{n}/{dist}/fp32"]["gbs"]
     return {"config": "tc", "metric": "tensor-core split-precision c2c GB/s vs plain FP32",
             "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "results": out}
+
+
+def ragged_accuracy(torch, np, d_out, flat, sizes, offs, count):
+    """Rel-L2 of `count` seeded transforms of a ragged output against the oracle, grouped by length."""
+    from paper_2207_06803_gb300 import synth
+    pick = synth.sample_rows(synth.DEFAULT_SEED + 11, sizes.size, count)
+    y_all = d_out.cpu().numpy().view(np.complex64)
+    errs, worst, passed, max_abs_n = [], {}, True, 0.0
+    for n in sorted(set(sizes[pick].tolist())):
+        sel = pick[sizes[pick] == n]
+        idx = offs[sel][:, None] + np.arange(n)[None, :]
+        a = accuracy_vs_oracle(y_all[idx], flat[idx], -1, gate(n, FP32_GATE))
+        worst[str(n)] = a["rel_l2_max"]
+        passed = passed and a["pass"]
+        max_abs_n = max(max_abs_n, a["max_abs_over_n"])
+        errs.append(a["rel_l2_max"])
+    return {"transforms": int(pick.size), "rel_l2_max_per_size": worst, "rel_l2_max": float(max(errs)),
+            "max_abs_over_n": max_abs_n, "gate": "2e-7 * log2(n) per size", "pass": passed}
 
 
 def run_ragged(args):
@@ -758,6 +904,7 @@ def run_ragged(args):
         ms1 = _time_ms(torch, lambda: rp.execute(d_in, d_out, stream), reps, stream)
         res["ragged_graph_default_us"] = 1e3 * ms0
         res["ragged_graph_tuned_us"] = 1e3 * ms1
+        res["oracle"] = ragged_accuracy(torch, np, d_out, flat, sizes, offs, 512)
         res["ragged_gbs"] = nbytes / (ms1 * 1e-3) / 1e9
         res["items"] = rp.num_items()
         res["engines"] = {str(n): gbfft.gbfft_ragged_engine(rp.handle, int(n)) for n in sorted(set(sizes.tolist()))}
@@ -878,7 +1025,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "sweep":
-        fn = {"twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving, "pease": run_pease,
+        fn = {"pr1": run_pr1, "twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving, "pease": run_pease,
               "f64": run_f64, "nd": run_nd}[args.config]
         print(json.dumps(fn(args)), flush=True)
         return 0
