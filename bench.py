@@ -458,7 +458,8 @@ def other_configs(args):
     small.steps = 40
     for name, fn in (("pr1", run_pr1), ("twopass", run_twopass), ("tc", lambda a: run_tc(a, dists=("uniform",))),
                      ("ragged", run_ragged), ("f64", run_f64), ("nd", run_nd),
-                     ("serving", lambda a: run_serving(a, rates=(1000, 10000), scale=0.2, serial_rates=(1000,)))):
+                     ("serving", lambda a: run_serving(a, rates=(1000, 10000, 50000), scale=0.2, serial_rates=(1000,),
+                                              per_length_rates=(10000,)))):
         try:
             r = fn(small)
         except Exception as e:  # a failing secondary measurement must not lose the headline line
@@ -491,8 +492,10 @@ def other_configs(args):
             out[name] = {k: r[k] for k in ("us", "gbs", "oracle", "cpu_naive_1core_s", "cpu_naive_all_cores_s")}
         else:
             out[name] = {"batching": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s", "gb_per_s",
-                                                               "service_over_10ms")}
+                                                               "service_over_10ms", "over_10ms_by_phase", "groups")}
                                       for rate, v in r["batching"].items()},
+                         "per_length_groups": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s", "groups")}
+                                               for rate, v in r["per_length_groups"].items()},
                          "serial_queue": {rate: {k: v[k] for k in ("p50_s", "p99_s", "req_per_s")}
                                           for rate, v in r["serial_queue"].items()}}
     return out
@@ -955,9 +958,15 @@ def run_ragged(args):
     return {"config": "ragged", "metric": "ragged batch GB/s on sum(16*N_i)", "unit": "GB/s", "results": res}
 
 
-def run_serving(args, rates=(1000, 2000, 5000, 10000, 20000, 50000), scale=1.0, serial_rates=(1000, 5000)):
+def run_serving(args, rates=(1000, 2000, 5000, 10000, 20000, 50000), scale=1.0, serial_rates=(1000, 5000),
+                per_length_rates=(10000, 50000)):
     """Open-loop Poisson arrivals; each request batch ~ U{1..256}, N uniform over
-    {2^k,3*2^k,5*2^k,7*2^k} in [16, 16384]; 4 GiB budget; continuous batching vs the serial queue."""
+    {2^k,3*2^k,5*2^k,7*2^k} in [16, 16384]; 4 GiB budget; page-locked host buffers.  Continuous
+    batching with one ragged launch per admission round and direction (lengths <= 8192) that reads
+    and writes the host buffers directly, against the same with the rows copied through the device
+    arena (staged), per-length groups and the serial queue.  Every group is timed by events (copies in, transform, copies out), so each request's
+    latency splits into phases, and a request whose service exceeded 10 ms is attributed to its
+    longest phase."""
     import numpy as np
     import torch
     from paper_2207_06803_gb300 import gbfft, synth
@@ -973,9 +982,9 @@ def run_serving(args, rates=(1000, 2000, 5000, 10000, 20000, 50000), scale=1.0, 
         t_in.append(torch.from_numpy(x.view(np.float32)).pin_memory())
         t_out.append(torch.empty_like(t_in[-1]).pin_memory())
     budget = 4 << 30
-    results = {}
+    phase_names = ("host_s", "device_wait_s", "h2d_s", "kernel_s", "d2h_s", "observe_s")
 
-    def drive(srv, rate, count, seed):
+    def drive(srv, rate, count, seed, timed):
         r = np.random.Generator(np.random.Philox(key=seed))
         pick = r.integers(0, templates, size=count)
         arr = np.cumsum(r.exponential(1.0 / rate, size=count))
@@ -987,37 +996,49 @@ def run_serving(args, rates=(1000, 2000, 5000, 10000, 20000, 50000), scale=1.0, 
             srv.wait(t, 300.0)
         st = srv.stats()
         tm = np.array([srv.timing(t) for t in tickets])
+        ph = [srv.phases(t) for t in tickets] if timed else None
         for t in tickets:
             srv.release(t)
         q, lat = tm[:, 0], tm[:, 1]
         service = lat - q
         st.update({"p999_s": float(np.percentile(lat, 99.9)), "queue_p99_s": float(np.percentile(q, 99)),
-                   # requests whose device-side service (copies in, transform, copies out) took over 10 ms:
-                   # a non-zero count marks a pause of the device or driver during the run
+                   # requests whose service (admission to completion seen) took over 10 ms
                    "service_over_10ms": int((service > 0.01).sum()),
                    "max_service_s": float(service.max())})
+        if timed:
+            mat = np.array([[p[k] for k in phase_names] for p in ph])
+            st["phase_p50_s"] = {k: float(np.percentile(mat[:, i], 50)) for i, k in enumerate(phase_names)}
+            st["phase_p99_s"] = {k: float(np.percentile(mat[:, i], 99)) for i, k in enumerate(phase_names)}
+            slow = np.where(service > 0.01)[0]
+            st["over_10ms_by_phase"] = {}
+            for j in slow:
+                k = phase_names[int(np.argmax(mat[j]))]
+                st["over_10ms_by_phase"][k] = st["over_10ms_by_phase"].get(k, 0) + 1
         return st
 
-    with gbfft.Server(mem_budget_bytes=budget, n_streams=4) as srv:
-        for n in fam.tolist():
-            srv.prepare(int(n), -1)
-        drive(srv, 5000, 1000, 7)  # warm-up
-        for rate in rates:
-            count = max(500, int(scale * (20000 if rate >= 5000 else 10 * rate)))
-            st = drive(srv, rate, count, rate)
-            results[str(rate)] = dict(st, requests=count, offered_req_per_s=rate)
-    serial = {}
-    with gbfft.Server(mem_budget_bytes=budget, n_streams=1, serial=True) as srv:
-        for n in fam.tolist():
-            srv.prepare(int(n), -1)
-        drive(srv, 1000, 500, 8)
-        for rate in serial_rates:
-            count = max(500, int(scale * 3000))
-            st = drive(srv, rate, count, rate + 1)
-            serial[str(rate)] = dict(st, requests=count, offered_req_per_s=rate)
+    def run_server(rates_, n_streams, warm_seed, count_of, **kw):
+        out = {}
+        timed = kw.get("phases", False)
+        with gbfft.Server(mem_budget_bytes=budget, n_streams=n_streams, **kw) as srv:
+            for n in fam.tolist():
+                srv.prepare(int(n), -1)
+            drive(srv, 5000, 1000, warm_seed, timed)  # warm-up
+            for rate in rates_:
+                count = count_of(rate)
+                st = drive(srv, rate, count, rate, timed)
+                out[str(rate)] = dict(st, requests=count, offered_req_per_s=rate)
+        return out
+
+    def count_full(rate):
+        return max(500, int(scale * (20000 if rate >= 5000 else 10 * rate)))
+
+    results = run_server(rates, 4, 7, count_full, phases=True)
+    per_length = run_server(per_length_rates, 4, 9, count_full, phases=True, per_length=True)
+    staged = run_server(per_length_rates, 4, 10, count_full, phases=True, staged=True)
+    serial = run_server(serial_rates, 1, 8, lambda rate: max(500, int(scale * 3000)), serial=True)
     return {"config": "serving", "metric": "serving p50/p99 latency (s) and throughput",
             "budget_bytes": budget, "streams": 4, "request_templates": templates,
-            "batching": results, "serial_queue": serial}
+            "batching": results, "staged_copies": staged, "per_length_groups": per_length, "serial_queue": serial}
 
 
 def main():

@@ -402,25 +402,51 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
  *
  * gbfft_server_create: `mem_budget_bytes` of device memory is reserved once
  * (one cudaMalloc) as the arena every admitted request's slot comes from;
- * `n_streams` (1..64) streams carry the groups; flags GBFFT_SERVER_SERIAL
- * turns batching off (one request in flight, one stream: the naive queue).
+ * `n_streams` (1..64) streams carry the groups.  Flags: GBFFT_SERVER_SERIAL
+ * turns batching off (one request in flight, one stream: the naive queue);
+ * GBFFT_SERVER_PHASES records timing events around every group's copies in,
+ * transform and copies out (gbfft_server_phases); GBFFT_SERVER_PER_LENGTH
+ * groups requests by (n, direction) only, without ragged launches;
+ * GBFFT_SERVER_STAGED always copies rows through the arena (see below).
  * gbfft_server_submit queues a request - `batch` rows of length n (any length
- * gbfft_plan_create supports), direction, HOST input and output buffers of
- * 8*n*batch bytes each (page-locked for overlap; they must stay valid until
- * the request completes) - stamps its arrival time and returns a ticket.
- * BUDGET if the request alone exceeds the arena, UNSUPPORTED_SIZE for lengths
- * with no plan.  The worker admits queued requests in FIFO order while their
- * slots fit in the arena, groups the admitted ones by (n, direction) into one
- * contiguous slot and one transform launch each, on the next stream of the
- * pool: requests arriving while earlier groups run are admitted as memory
- * frees up and overlap them.  Schedules and twiddle tables are built once per
- * (n, direction) and stay resident (gbfft_server_prepare builds them ahead).
- * An event recorded after each group's copies back, polled by the worker,
- * stamps completion; latency is completion - arrival.
+ * gbfft_plan_create supports), direction, input and output buffers of
+ * 8*n*batch bytes each, in host memory (page-locked for overlap) or device
+ * memory (the copies use the unified address space: cudaMemcpyDefault); they
+ * must stay valid until the request completes - stamps its arrival time and
+ * returns a ticket.  BUDGET if the request alone exceeds the arena,
+ * UNSUPPORTED_SIZE for lengths with no plan.  The worker admits queued
+ * requests in FIFO order while their slots fit in the arena.  Admitted
+ * requests of lengths n <= 8192 with prime factors 2, 3, 5, 7 are batched
+ * across lengths: per direction, one slot holds all of them and ONE launch of
+ * the persistent ragged kernel (gbfft_plan_ragged's kernel, its queue of
+ * (length, rows) items built on the host and uploaded with one copy)
+ * transforms every row.  When a request's input and output are both
+ * device-visible (device memory, or page-locked host memory mapped into the
+ * device's address space, which on a Grace-Blackwell node the GPU reaches
+ * over NVLink-C2C) the launch reads and writes them in place where they are,
+ * with no copies and no arena bytes for its rows; otherwise its rows are
+ * copied into the slot, transformed there and copied back.  Input and output
+ * must then not overlap partially (the same buffer is fine).  The other
+ * lengths are grouped by
+ * (n, direction) into one slot and one launch each.  Each group runs on the
+ * next stream of the pool: requests arriving while earlier groups run are
+ * admitted as memory frees up and overlap them.  Schedules, ragged length
+ * descriptors and twiddle tables are built once per length and stay resident
+ * (gbfft_server_prepare builds them ahead).  An event recorded after each
+ * group's copies back, polled by the worker, stamps completion; latency is
+ * completion - arrival.
  * gbfft_server_poll: *done = 1 finished, 0 pending, -1 failed/cancelled;
  * *latency_s once finished.  gbfft_server_timing splits a finished request's
  * latency: *queued_s = admission - arrival (waiting in the server's queue),
  * *latency_s as gbfft_server_poll (INVALID_ARG until finished).
+ * gbfft_server_phases fills out8 for a finished request (INVALID_ARG until
+ * then) with the phases of its service in seconds: {queued (admission -
+ * arrival), host (the worker issuing the group's copies and launches), device
+ * wait (start of the group's first copy on the device - end of that issue),
+ * copies in, transform, copies out, observe (the worker seeing the completion
+ * - end of the copies back on the device), latency}; device-side phases are
+ * placed on the host clock through an event recorded at server creation, and
+ * are NaN unless the server was created with GBFFT_SERVER_PHASES.
  * gbfft_server_wait blocks up to timeout_s
  * (TIMEOUT otherwise).  gbfft_server_release forgets a finished ticket.
  * gbfft_server_replay submits `count` requests at arrival offsets arrival_s[i]
@@ -435,13 +461,17 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
  */
 typedef struct gbfft_server_s *gbfft_server;
 #define GBFFT_SERVER_SERIAL 1
+#define GBFFT_SERVER_PHASES 2
+#define GBFFT_SERVER_PER_LENGTH 4
+#define GBFFT_SERVER_STAGED 8
 
 gbfft_status gbfft_server_create(gbfft_server *out, size_t mem_budget_bytes, int n_streams, int flags);
 gbfft_status gbfft_server_prepare(gbfft_server srv, int64_t n, int direction);
-gbfft_status gbfft_server_submit(gbfft_server srv, int64_t n, int64_t batch, int direction, const void *host_in,
-                                 void *host_out, uint64_t *ticket);
+gbfft_status gbfft_server_submit(gbfft_server srv, int64_t n, int64_t batch, int direction, const void *host_or_dev_in,
+                                 void *host_or_dev_out, uint64_t *ticket);
 gbfft_status gbfft_server_poll(gbfft_server srv, uint64_t ticket, int *done, double *latency_s);
 gbfft_status gbfft_server_timing(gbfft_server srv, uint64_t ticket, double *queued_s, double *latency_s);
+gbfft_status gbfft_server_phases(gbfft_server srv, uint64_t ticket, double *out8);
 gbfft_status gbfft_server_wait(gbfft_server srv, uint64_t ticket, double timeout_s);
 gbfft_status gbfft_server_release(gbfft_server srv, uint64_t ticket);
 gbfft_status gbfft_server_replay(gbfft_server srv, int64_t count, const int64_t *n, const int64_t *batch,

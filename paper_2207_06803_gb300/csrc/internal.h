@@ -125,6 +125,24 @@ int ragged_class_split(const RaggedState* r, int64_t n);
 int ragged_queue_order(const RaggedState* r);
 gbfft_status ragged_set_engine(RaggedState* r, int64_t n, int compiled);
 int ragged_engine(const RaggedState* r, int64_t n);
+
+// Length table and per-call queues for ragged launches whose transforms change
+// from call to call (ragged.cu).
+struct RaggedTable;
+struct RaggedSpan {
+    int64_t n;     // transform length
+    long long off; // complex element of the first row in the data buffer
+    int64_t rows;  // consecutive rows of length n
+    long long dout; // the output rows start dout complex elements after the input rows
+};
+gbfft_status ragged_table_create(RaggedTable** out);
+void ragged_table_destroy(RaggedTable* t);
+gbfft_status ragged_table_add(RaggedTable* t, int64_t n, cudaStream_t s, int* cls);
+size_t ragged_blob_bytes(int64_t nitems, int64_t nrows);
+int64_t ragged_table_build(const RaggedTable* t, const RaggedSpan* spans, int64_t nspans, char* blob, size_t cap,
+                           size_t* bytes);
+cudaError_t ragged_table_launch(const RaggedTable* t, int direction, float2* data, const char* d_blob,
+                                int64_t nitems, int* status, cudaStream_t s);
 // Radix schedule the plan uses for length n (stage count; 0 if n is absent).
 int ragged_schedule(const RaggedState* r, int64_t n, int* radix);
 bool ragged_supported(int64_t n);

@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -187,7 +189,7 @@ static gbfft_status ragged_build_items(RaggedState* r) {
         });
     }
     for (const Pending& p : pend) {
-        RaggedItem it;
+        RaggedItem it{};
         it.cls = p.cls;
         it.count = (int)p.rows.size();
         it.first = (int)r->row_offs.size();
@@ -535,6 +537,172 @@ bool ragged_supported(int64_t n) {
     for (int p : {2, 3, 5, 7})
         while (n % p == 0) n /= p;
     return n == 1;
+}
+
+
+// ---------------------------------------------------------------------------
+// Length table and per-call queues: ragged launches whose set of transforms
+// changes from call to call (the serving loop's admission rounds).  The table
+// keeps one descriptor and one schedule's twiddle blocks per length, resident
+// and append-only (a kernel in flight never sees an entry change); each call
+// packs its queue entries and row offsets into one blob that a single copy
+// uploads, counter included.
+// ---------------------------------------------------------------------------
+
+namespace {
+constexpr int kTableMaxLens = 1024;
+constexpr size_t kTableTwCap = size_t(1) << 22;  // float2 entries of twiddle blocks (32 MiB)
+constexpr long long kTableWaitNs = 200000000LL;  // bound on a ready-wait (every entry is published ready)
+}  // namespace
+
+struct RaggedTable {
+    std::vector<RaggedLenState> lens;
+    std::map<int64_t, int> cls_of;
+    RaggedLen* d_lens = nullptr;
+    float2* d_tw = nullptr;
+    size_t tw_used = 0;
+    int grid = 0;
+};
+
+void ragged_table_destroy(RaggedTable* t) {
+    if (!t) return;
+    if (t->d_lens) cudaFree(t->d_lens);
+    if (t->d_tw) cudaFree(t->d_tw);
+    delete t;
+}
+
+gbfft_status ragged_table_create(RaggedTable** out) {
+    *out = nullptr;
+    RaggedTable* t = new (std::nothrow) RaggedTable();
+    if (!t) return GBFFT_ERR_OOM;
+    if (cudaMalloc(&t->d_lens, sizeof(RaggedLen) * kTableMaxLens) != cudaSuccess ||
+        cudaMalloc(&t->d_tw, sizeof(float2) * kTableTwCap) != cudaSuccess) {
+        cudaGetLastError();
+        ragged_table_destroy(t);
+        return GBFFT_ERR_OOM;
+    }
+    const void* ks[2] = {ragged_kernel_fwd(), ragged_kernel_inv()};
+    int dev = 0, sms = 0, per_sm = 0;
+    for (const void* k : ks)
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kRaggedSmemBytes) != cudaSuccess) {
+            ragged_table_destroy(t);
+            return GBFFT_ERR_CUDA;
+        }
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks[0], kRaggedThreads, (size_t)kRaggedSmemBytes) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        ragged_table_destroy(t);
+        return GBFFT_ERR_CUDA;
+    }
+    t->grid = per_sm * sms;
+    *out = t;
+    return GBFFT_OK;
+}
+
+// The entry of length n, added (descriptor uploaded, twiddles generated on
+// `s`, then synchronised) if it is new.  UNSUPPORTED_SIZE if n is not a
+// 7-smooth length <= 8192, OOM if the table is full.
+gbfft_status ragged_table_add(RaggedTable* t, int64_t n, cudaStream_t s, int* cls) {
+    auto it = t->cls_of.find(n);
+    if (it != t->cls_of.end()) {
+        *cls = it->second;
+        return GBFFT_OK;
+    }
+    if (!ragged_supported(n)) return GBFFT_ERR_UNSUPPORTED_SIZE;
+    if ((int)t->lens.size() >= kTableMaxLens) return GBFFT_ERR_OOM;
+    RaggedLenState L;
+    L.n = n;
+    std::vector<std::vector<int>> cands = schedules_of(n);
+    L.body = ragged_body_id((int)n);
+    std::vector<int> sch = cands.empty() ? std::vector<int>() : cands[0];
+    if (L.body >= 0) {
+        sch.clear();
+        for (int r : kRaggedBodies[L.body].radix)
+            if (r > 0) sch.push_back(r);
+        L.body_cand = 0;
+        L.use_body = 1;
+    }
+    L.cands = {sch};
+    const int cnt = stage_twiddle_count(sch.data(), (int)sch.size());
+    if (t->tw_used + (size_t)std::max(cnt, 1) > kTableTwCap) return GBFFT_ERR_OOM;
+    L.tw_base = {(int)t->tw_used};
+    const RaggedLen desc = describe(L);
+    const int c = (int)t->lens.size();
+    if (cnt > 0 && launch_stage_twiddles(t->d_tw + t->tw_used, n, sch.data(), (int)sch.size(), s) != cudaSuccess)
+        return GBFFT_ERR_CUDA;
+    if (cudaMemcpyAsync(t->d_lens + c, &desc, sizeof(RaggedLen), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GBFFT_ERR_CUDA;
+    t->tw_used += (size_t)std::max(cnt, 1);
+    t->lens.push_back(L);
+    t->cls_of[n] = c;
+    *cls = c;
+    return GBFFT_OK;
+}
+
+size_t ragged_blob_bytes(int64_t nitems, int64_t nrows) {
+    return 16 + sizeof(RaggedItem) * (size_t)nitems + sizeof(long long) * (size_t)nrows;
+}
+
+// Queue entries for `nspans` spans of consecutive rows (every span's length
+// already in the table), heaviest entry first, packed into `blob` (at most
+// `cap` bytes): a zero counter, the entries, the row offsets.  Returns the
+// entry count, or -1 if the blob would not fit.
+int64_t ragged_table_build(const RaggedTable* t, const RaggedSpan* spans, int64_t nspans, char* blob, size_t cap,
+                           size_t* bytes) {
+    std::vector<RaggedItem> items;
+    std::vector<double> cost;
+    int64_t nrows = 0;
+    for (int64_t k = 0; k < nspans; ++k) {
+        const RaggedLenState& L = t->lens[t->cls_of.at(spans[k].n)];
+        const int64_t per = rows_per_item(L);
+        for (int64_t r0 = 0; r0 < spans[k].rows; r0 += per) {
+            RaggedItem it{};
+            it.dout = spans[k].dout;
+            it.cls = t->cls_of.at(spans[k].n);
+            it.count = (int)std::min(per, spans[k].rows - r0);
+            it.first = (int)(nrows + r0);
+            it.ready = 1;
+            items.push_back(it);
+            cost.push_back((double)it.count * (double)L.n * std::max(1.0, std::log2((double)L.n)));
+        }
+        nrows += spans[k].rows;
+    }
+    const size_t need = ragged_blob_bytes((int64_t)items.size(), nrows);
+    if (need > cap) return -1;
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::memset(blob, 0, 16);
+    RaggedItem* bi = reinterpret_cast<RaggedItem*>(blob + 16);
+    for (size_t i = 0; i < order.size(); ++i) bi[i] = items[order[i]];
+    long long* bo = reinterpret_cast<long long*>(blob + 16 + sizeof(RaggedItem) * items.size());
+    for (int64_t k = 0, row = 0; k < nspans; ++k)
+        for (int64_t r = 0; r < spans[k].rows; ++r) bo[row++] = spans[k].off + r * spans[k].n;
+    *bytes = need;
+    return (int64_t)items.size();
+}
+
+// One persistent launch over a blob already on the device (`d_blob`, as
+// packed by ragged_table_build), transforming the rows of `data` in place.
+cudaError_t ragged_table_launch(const RaggedTable* t, int direction, float2* data, const char* d_blob,
+                                int64_t nitems, int* status, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    const float2* pin = data;
+    float2* pout = data;
+    const RaggedItem* items = reinterpret_cast<const RaggedItem*>(d_blob + 16);
+    int n_items = (int)nitems;
+    const long long* offs = reinterpret_cast<const long long*>(d_blob + 16 + sizeof(RaggedItem) * (size_t)nitems);
+    const RaggedLen* lens = t->d_lens;
+    const float2* tw = t->d_tw;
+    int* counter = reinterpret_cast<int*>(const_cast<char*>(d_blob));
+    long long wait_ns = kTableWaitNs;
+    void* args[10] = {(void*)&pin, (void*)&pout, (void*)&items, (void*)&n_items, (void*)&offs,
+                      (void*)&lens, (void*)&tw,  (void*)&counter, (void*)&status, (void*)&wait_ns};
+    const void* fn = direction == GBFFT_FORWARD ? ragged_kernel_fwd() : ragged_kernel_inv();
+    const int grid = (int)std::min<int64_t>(t->grid, nitems);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kRaggedThreads), args, (size_t)kRaggedSmemBytes, s);
 }
 
 }  // namespace gbfft

@@ -42,10 +42,12 @@ constexpr int kRaggedMaxN = 8192;
 constexpr int kRaggedSmemBytes = (int)sizeof(float2) * (kRaggedTile + kRaggedTile / 16);
 
 struct RaggedItem {
-    int cls;    // index of the item's length descriptor
-    int count;  // rows in this item (<= T of the length)
-    int first;  // index of the item's first row offset in the offset list
-    int ready;  // nonzero once the item may be processed
+    int cls;         // index of the item's length descriptor
+    int count;       // rows in this item (<= T of the length)
+    int first;       // index of the item's first row offset in the offset list
+    int ready;       // nonzero once the item may be processed
+    long long dout;  // the item's output rows start dout complex elements after its input rows' offsets
+    long long pad;
 };
 
 // One stage of a length's schedule: radix R, L = R_1 ... R_{s-1}, n/R
@@ -68,7 +70,7 @@ struct RaggedLen {
 };
 static_assert(sizeof(RaggedLen) % 16 == 0, "descriptors are copied in 16-byte pieces");
 constexpr int kRaggedLenChunks = (int)(sizeof(RaggedLen) / 16);
-static_assert(sizeof(RaggedItem) == 16, "queue entries are copied in one 16-byte piece");
+static_assert(sizeof(RaggedItem) == 32, "queue entries are copied in two 16-byte pieces");
 
 // Compiled schedules.  For the lengths n = p * 2^k (p = 1, 3, 5, 7, 8 <= n <=
 // 8192) an item runs a schedule fixed at compile time: the single-pass stage
@@ -349,7 +351,10 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
         for (int k = 0; k < 2; ++k) {
             const int id = claim();
             s_id[k] = id;
-            if (id < nitems) ragged_cp_async16(&s_item[k], items + id);
+            if (id < nitems) {
+                ragged_cp_async16(&s_item[k], items + id);
+                ragged_cp_async16(reinterpret_cast<char*>(&s_item[k]) + 16, reinterpret_cast<const char*>(items + id) + 16);
+            }
         }
         ragged_cp_async_wait();
     }
@@ -379,22 +384,27 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
         const int it = s_id[cur];
         if (it >= nitems) break;
         const int count = s_item[cur].count;
+        float2* const iout = out + s_item[cur].dout;  // this item's output rows (off[t] from here)
         if (s_id[nxt] < nitems) fetch(s_item[nxt], ls ^ 1);
         if (tid == 0) {
             const int id = claim();
             s_id[aft] = id;
-            if (id < nitems) ragged_cp_async16(&s_item[aft], items + id);
+            if (id < nitems) {
+                ragged_cp_async16(&s_item[aft], items + id);
+                ragged_cp_async16(reinterpret_cast<char*>(&s_item[aft]) + 16,
+                                  reinterpret_cast<const char*>(items + id) + 16);
+            }
         }
         if (!s_ok) continue;
         const long long* off = s_off[ls];
         const int body = s_len[ls].body;
         if (body >= 0) {
-            ragged_compiled<S>(body, in, out, off, sm, tw + s_len[ls].tw0, count);
+            ragged_compiled<S>(body, in, iout, off, sm, tw + s_len[ls].tw0, count);
             continue;
         }
         const int n = s_len[ls].n, ns = s_len[ls].nstages;
         if (ns == 0) {  // n == 1: DFT_1 is the identity
-            for (int t = tid; t < count; t += kRaggedThreads) out[off[t]] = in[off[t]];
+            for (int t = tid; t < count; t += kRaggedThreads) iout[off[t]] = in[off[t]];
             continue;
         }
         // A one-stage schedule (n <= 16) also goes through the tile, then a
@@ -403,13 +413,13 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
             const RaggedStage st = s_len[ls].st[s];
             const bool src_smem = s > 0, dst_smem = s < ns - 1 || ns == 1;
             switch (st.r) {
-                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
-                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
-                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
-                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
-                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
-                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
-                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, out, off, sm, tw, st, n, count); break;
+                case 2: ragged_stage<S, 2>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
+                case 3: ragged_stage<S, 3>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
+                case 4: ragged_stage<S, 4>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
+                case 5: ragged_stage<S, 5>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
+                case 7: ragged_stage<S, 7>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
+                case 8: ragged_stage<S, 8>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
+                case 16: ragged_stage<S, 16>(src_smem, dst_smem, in, iout, off, sm, tw, st, n, count); break;
                 default:
                     if (tid == 0) atomicCAS(status, 0, (int)GBFFT_ERR_DEVICE_STATUS);
                     break;
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
             const unsigned mag_n = s_len[ls].mag_n;
             for (int idx = tid; idx < count * n; idx += kRaggedThreads) {
                 const int t = rdiv(idx, mag_n), j = idx - t * n;
-                out[off[t] + j] = sm[rpad(idx)];
+                iout[off[t] + j] = sm[rpad(idx)];
             }
         }
     }

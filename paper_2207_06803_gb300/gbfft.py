@@ -84,6 +84,7 @@ PROTOTYPES = {
     "gbfft_ragged_engine": (_c_int, [_c_vp, _c_i64]),
     "gbfft_plan_create_nd": (_c_int, [ctypes.POINTER(_c_vp), _c_int, _c_i64p, _c_i64, _c_int, _c_int]),
     "gbfft_plan_dims": (_c_int, [_c_vp, _c_intp, _c_i64p]),
+    "gbfft_server_phases": (_c_int, [_c_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double)]),
     "gbfft_server_timing": (_c_int, [_c_vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double)]),
     "gbfft_formula_check": (_c_int, [ctypes.c_char_p, _c_i64p, _c_intp, _c_int, _c_intp, _c_i64p, ctypes.c_char_p,
@@ -107,6 +108,10 @@ PROTOTYPES = {
     "gbfft_server_destroy": (_c_int, [_c_vp]),
 }
 GBFFT_SERVER_SERIAL = 1
+GBFFT_SERVER_PHASES = 2
+GBFFT_SERVER_PER_LENGTH = 4
+GBFFT_SERVER_STAGED = 8
+SERVER_PHASES = ("queued_s", "host_s", "device_wait_s", "h2d_s", "kernel_s", "d2h_s", "observe_s", "latency_s")
 SERVER_STATS = ("completed", "p50_s", "p99_s", "max_s", "req_per_s", "gb_per_s", "groups",
                 "max_inflight_requests", "max_arena_bytes", "window_s")
 
@@ -445,6 +450,12 @@ def gbfft_server_poll(srv: int, ticket: int) -> tuple[int, float]:
     return done.value, lat.value
 
 
+def gbfft_server_phases(srv: int, ticket: int) -> dict:
+    out = (ctypes.c_double * 8)()
+    _check(lib().gbfft_server_phases(srv, ticket, out), "gbfft_server_phases")
+    return dict(zip(SERVER_PHASES, list(out)))
+
+
 def gbfft_server_timing(srv: int, ticket: int) -> tuple[float, float]:
     """(seconds queued before admission, total latency) of a finished request."""
     q, lat = ctypes.c_double(), ctypes.c_double()
@@ -488,10 +499,13 @@ def gbfft_server_destroy(srv: int) -> None:
 
 
 class Server:
-    """Continuous-batching FFT server (see include/gbfft.h); host buffers in/out."""
+    """Continuous-batching FFT server (see include/gbfft.h); host or device buffers in/out."""
 
-    def __init__(self, mem_budget_bytes: int = 4 << 30, n_streams: int = 4, serial: bool = False):
-        self.handle = gbfft_server_create(mem_budget_bytes, n_streams, GBFFT_SERVER_SERIAL if serial else 0)
+    def __init__(self, mem_budget_bytes: int = 4 << 30, n_streams: int = 4, serial: bool = False,
+                 phases: bool = False, per_length: bool = False, staged: bool = False):
+        flags = ((GBFFT_SERVER_SERIAL if serial else 0) | (GBFFT_SERVER_PHASES if phases else 0)
+                 | (GBFFT_SERVER_PER_LENGTH if per_length else 0) | (GBFFT_SERVER_STAGED if staged else 0))
+        self.handle = gbfft_server_create(mem_budget_bytes, n_streams, flags)
 
     def prepare(self, n: int, direction: int = GBFFT_FORWARD) -> None:
         gbfft_server_prepare(self.handle, n, direction)
@@ -504,6 +518,9 @@ class Server:
 
     def timing(self, ticket: int) -> tuple[float, float]:
         return gbfft_server_timing(self.handle, ticket)
+
+    def phases(self, ticket: int) -> dict:
+        return gbfft_server_phases(self.handle, ticket)
 
     def wait(self, ticket: int, timeout_s: float = 60.0) -> None:
         gbfft_server_wait(self.handle, ticket, timeout_s)

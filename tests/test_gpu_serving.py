@@ -46,8 +46,9 @@ def test_mix_equals_alone_and_oracle():
         assert st["completed"] == len(ns)
         assert 0 < st["p50_s"] <= st["p99_s"] <= st["max_s"]
         assert st["groups"] <= len(ns) and st["max_arena_bytes"] <= (256 << 20)
-    # each request alone, through a server that runs one request at a time
-    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=1, serial=True) as alone:
+    # each request alone, through the same kind of server with nothing else in flight (a request's rows
+    # are cut into the same queue items whatever else shares the launch)
+    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=1) as alone:
         for i in range(len(ns)):
             solo = torch.full_like(ins[i], float("nan")).pin_memory()
             alone.wait(alone.submit(int(ns[i]), int(bs[i]), int(dirs[i]), ins[i], solo), 60.0)
@@ -98,3 +99,73 @@ def test_destroy_with_work_outstanding_does_not_hang():
         if 16 * n * b + 512 <= (16 << 20):
             srv.submit(int(n), int(b), int(d), i, o)
     srv.close()  # cancels what is queued, waits for what runs
+
+
+def test_serial_and_per_length_servers_agree_with_the_oracle():
+    """The naive queue (one request at a time) and per-length batching run the
+    single-pass / two-pass kernels instead of the ragged launch: bit for bit
+    the same as each other, and within tolerance of the oracle."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    ns, bs, dirs, ins, outs = make_requests(40, SEED + 3)
+    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=3, per_length=True) as srv:
+        for t in srv.replay(ns, bs, dirs, ins, outs, np.linspace(0, 0.01, len(ns))):
+            srv.wait(t, 60.0)
+        assert srv.stats()["completed"] == len(ns)
+    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=1, serial=True) as alone:
+        for i in range(len(ns)):
+            solo = torch.full_like(ins[i], float("nan")).pin_memory()
+            alone.wait(alone.submit(int(ns[i]), int(bs[i]), int(dirs[i]), ins[i], solo), 60.0)
+            assert torch.equal(solo, outs[i]), i
+    for i in range(0, len(ns), 3):
+        n, b = int(ns[i]), int(bs[i])
+        x = ins[i].numpy().view(np.complex64).reshape(b, n)
+        ref = oracle.dft(x.astype(np.complex128), int(dirs[i]), nthreads=ncpu())
+        assert row_rel_l2(outs[i].numpy().view(np.complex64).reshape(b, n), ref).max() <= tol_fp32(n), (i, n)
+
+
+def test_device_buffers_and_phases():
+    """Requests whose input and output live in device memory, on a server
+    that times every group's phases: the results match host-buffer requests
+    bit for bit, and each request's phases add up to its latency."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    ns, bs, dirs, ins, outs = make_requests(48, SEED + 4)
+    d_ins = [t.cuda() for t in ins]
+    d_outs = [torch.full_like(t, float("nan")) for t in d_ins]
+    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=4, phases=True) as srv:
+        tickets = srv.replay(ns, bs, dirs, d_ins, d_outs, np.linspace(0, 0.01, len(ns)))
+        for t in tickets:
+            srv.wait(t, 60.0)
+        for t in tickets:
+            ph = srv.phases(t)
+            assert all(np.isfinite(v) for v in ph.values())
+            assert ph["h2d_s"] >= 0 and ph["kernel_s"] >= 0 and ph["d2h_s"] >= 0 and ph["queued_s"] >= 0
+            parts = sum(v for k, v in ph.items() if k != "latency_s")
+            assert abs(parts - ph["latency_s"]) <= 1e-6 + 1e-9 * ph["latency_s"]
+        for t in tickets:
+            srv.release(t)
+        for t in srv.replay(ns, bs, dirs, ins, outs, np.linspace(0, 0.01, len(ns))):
+            srv.wait(t, 60.0)
+    torch.cuda.synchronize()
+    for i in range(len(ns)):
+        assert torch.equal(d_outs[i].cpu(), outs[i]), i
+
+
+def test_direct_and_staged_ragged_launches_agree():
+    """Pinned host buffers are read and written by the ragged launch directly
+    (over the host link) or copied through the device arena (staged): the
+    same kernel on the same queue items, so the results agree bit for bit."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    ns, bs, dirs, ins, outs = make_requests(64, SEED + 6, hi=8192)
+    staged_out = [torch.full_like(t, float("nan")).pin_memory() for t in ins]
+    arrivals = np.linspace(0, 0.01, len(ns))
+    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=4) as srv:
+        for t in srv.replay(ns, bs, dirs, ins, outs, arrivals):
+            srv.wait(t, 60.0)
+    with gbfft.Server(mem_budget_bytes=256 << 20, n_streams=4, staged=True) as srv:
+        for t in srv.replay(ns, bs, dirs, ins, staged_out, arrivals):
+            srv.wait(t, 60.0)
+    for i in range(len(ns)):
+        assert torch.equal(staged_out[i], outs[i]), i
