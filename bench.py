@@ -525,7 +525,7 @@ def run_e2e(torch, np, flat, plans, stream, world, e2e_steps, calls):
     return {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
             "h2d_bytes_per_step": calls * BYTES_PER_CALL // 2,
             "d2h_bytes_per_step": calls * BYTES_PER_CALL // 2,
-            "path": "gbfft_execute_host (pinned host buffers, 32 MiB chunk ring)"}
+            "path": "gbfft_execute_host on pinned host buffers (the kernels read and write them directly over NVLink-C2C)"}
 
 
 # --------------------------------------------------------------------------

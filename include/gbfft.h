@@ -141,7 +141,11 @@ gbfft_status gbfft_execute(gbfft_plan p, const void *in, void *out, void *cuda_s
 
 /*
  * Host-buffer form of gbfft_execute: `in` and `out` are HOST pointers to
- * batch*n complex64 values (in == out allowed).  The batch is streamed through
+ * batch*n complex64 values (in == out allowed).  When both buffers are
+ * addressable by the device (page-locked host memory mapped into its address
+ * space - on a Grace-Blackwell node the GPU reaches it over NVLink-C2C - or
+ * device memory) and 16-byte aligned, the plan's kernels read and write them
+ * directly, with no staging.  Otherwise the batch is streamed through
  * a ring of three device staging buffers of about 32 MiB each (allocated by
  * the plan on the first call and kept until gbfft_destroy): the host-to-device
  * copy of one chunk, the transform of the previous chunk and the

@@ -659,7 +659,22 @@ gbfft_status gbfft_execute(gbfft_plan p, const void* in, void* out, void* cuda_s
 
 // Chunked host -> device -> host pipeline over a ring of staging buffers:
 // while chunk c is transformed on the caller's stream, chunk c+1 is being
-// copied in and chunk c-1 copied out on two internal streams.
+// copied in and chunk c-1 copied out on two internal streams.  Buffers the
+// device can address directly skip the ring (see device_address).
+
+// The address at which the device reaches `p` (device or managed memory, or
+// page-locked host memory mapped into the device's address space), or null.
+static const void* device_address(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeHost)
+        return a.devicePointer;
+    return nullptr;
+}
+
 gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_out, void* cuda_stream) {
     if (!p || !host_in || !host_out || p->kind == kPlanRagged) return GBFFT_ERR_INVALID_ARG;
     if (p->batch == 0) return GBFFT_OK;
@@ -668,6 +683,16 @@ gbfft_status gbfft_execute_host(gbfft_plan p, const void* host_in, void* host_ou
     if (host_in != host_out) {
         const uintptr_t a = (uintptr_t)host_in, b = (uintptr_t)host_out;
         if (a < b + bytes && b < a + bytes) return GBFFT_ERR_OVERLAP;
+    }
+    // Buffers the device can address (page-locked host memory mapped into its address space - reached
+    // over NVLink-C2C on a Grace-Blackwell node - or device memory): the plan's kernels read and write
+    // them directly, with no staging copies.
+    {
+        const void* din = device_address(host_in);
+        void* dout = const_cast<void*>(device_address(host_out));
+        if (din && dout && ((uintptr_t)din & 15u) == 0 && ((uintptr_t)dout & 15u) == 0)
+            return run_device(p, din, dout, p->batch, (cudaStream_t)cuda_stream) == cudaSuccess ? GBFFT_OK
+                                                                                              : GBFFT_ERR_CUDA;
     }
     constexpr size_t kChunkBytes = size_t(32) << 20;
     if (!p->stage[0]) {
