@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbfft", "reference"], default="gbfft")
-    ap.add_argument("--config", choices=["sweep", "pr1", "twopass", "tc", "ragged", "serving", "f64", "nd", "pease"],
+    ap.add_argument("--config", choices=["sweep", "pr1", "mixed", "twopass", "tc", "ragged", "serving", "f64", "nd", "pease"],
                     default="sweep",
                     help="sweep (default, the headline line) or one of the other configurations")
     ap.add_argument("--seed", type=int, default=None)
@@ -632,6 +632,46 @@ def run_pr1(args):
             "cpu_naive_1core_s": t1 - t0, "cpu_naive_all_cores_s": t2 - t1, "cpu_cores": cores}
 
 
+def run_mixed(args):
+    """Single-pass mixed-radix lengths p * 2^k (p = 3, 5, 7) from 10 to 3584, forward, about 2^26 points per
+    call: GB/s (16 B/point) of the default plan and of every compiled variant of the length, and the default
+    plan's error on 256 sampled rows against the FP64 oracle."""
+    import numpy as np
+    import torch
+    from paper_2207_06803_gb300 import gbfft, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    peak, src = _peak()
+    flat = synth.uniform_flat(synth.DEFAULT_SEED, 0, TOTAL)
+    d_in = torch.from_numpy(flat.view(np.float32)).cuda()
+    d_out = torch.empty_like(d_in)
+    sizes = [int(v) for v in args.sizes.split(",")] if args.sizes else \
+        [n for n in synth.size_family(10, 4096) if n & (n - 1)]
+    rows = {}
+    for n in sizes:
+        batch = TOTAL // n
+        res = {"batch": batch, "variants": {}}
+        with gbfft.Plan(n, batch, -1) as p:
+            info = p.info()
+            ms = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
+        gbs = 16.0 * n * batch / (ms * 1e-3) / 1e9
+        r_chk = synth.sample_rows(synth.DEFAULT_SEED + n, batch, 256)
+        res.update({"default_variant": info["variant"], "radices": info["radices"], "gbs": gbs,
+                    "frac_of_hbm": gbs / peak,
+                    "oracle": accuracy_vs_oracle(sampled_rows(torch, np, d_out, batch, n, r_chk),
+                                                 flat[: batch * n].reshape(batch, n)[r_chk], -1, gate(n, FP32_GATE))})
+        for v in range(gbfft.gbfft_num_variants(n)):
+            with gbfft.Plan(n, batch, -1, variant=v) as p:
+                msv = _time_ms(torch, lambda: p.execute(d_in, d_out, stream), max(5, args.steps // 40), stream)
+            vi = gbfft.gbfft_variant_info(n, v)
+            res["variants"][str(v)] = {"radices": vi["radices"], "rows_per_cta": vi["rows_per_cta"],
+                                       "threads": vi["threads_per_cta"], "kind": gbfft.gbfft_variant_kind(n, v),
+                                       "gbs": 16.0 * n * batch / (msv * 1e-3) / 1e9}
+        rows[str(n)] = res
+    return {"config": "mixed", "metric": "single-pass mixed-radix c2c GB/s (16 B/point) and oracle error",
+            "unit": "GB/s", "points_per_call": TOTAL, "peak_gbs": peak, "peak_source": src, "per_size": rows}
+
+
 def run_twopass(args):
     """Eq. 2 two-pass lengths 5120..16384 at 2^26 points per call."""
     import numpy as np
@@ -1046,7 +1086,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "sweep":
-        fn = {"pr1": run_pr1, "twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving, "pease": run_pease,
+        fn = {"pr1": run_pr1, "mixed": run_mixed, "twopass": run_twopass, "tc": run_tc, "ragged": run_ragged, "serving": run_serving, "pease": run_pease,
               "f64": run_f64, "nd": run_nd}[args.config]
         print(json.dumps(fn(args)), flush=True)
         return 0

@@ -1,5 +1,6 @@
 // Single-pass variants for lengths p * 2^k (p = 3, 5, 7) up to 4096: one
-// radix-p stage first, then power-of-two stages.  The first entry of each
+// radix-p stage first, then power-of-two stages.  From 10 to 56 the default is
+// the one-row-per-thread kernel (GBFFT_SMALL2).  Above, the first entry of each
 // length (GBFFT_ROWS_T: explicit thread count, sized by the radix-16 stages;
 // the radix-p stage runs ceil(butterflies/threads) per thread) is the
 // default; the GBFFT_ROWS entries (E a multiple of every radix) remain as
@@ -9,6 +10,17 @@
 namespace gbfft {
 
 static const RowsVariant kMixed[] = {
+    // N = 10 ... 56: one row per thread, both Stockham stages in registers, the tile staged through shared
+    // memory with 16-byte accesses (the defaults: 6.1-6.8 TB/s against 5.1-6.4 for the tile kernels below)
+    GBFFT_SMALL2(10, 128, 5, 2),
+    GBFFT_SMALL2(12, 128, 3, 4),
+    GBFFT_SMALL2(14, 128, 7, 2),
+    GBFFT_SMALL2(20, 128, 5, 4),
+    GBFFT_SMALL2(24, 128, 3, 8),
+    GBFFT_SMALL2(28, 128, 7, 4),
+    GBFFT_SMALL2(40, 64, 5, 8),
+    GBFFT_SMALL2(48, 64, 3, 16),
+    GBFFT_SMALL2(56, 64, 7, 8),
     // N = 4 as two radix-2 stages (Eq. 1's factorisation; an alternative to the radix-4 codelet)
     GBFFT_ROWS(4, 4, 128, 0, 2, 2),
     GBFFT_ROWS(3, 3, 128, 0, 3),

@@ -513,4 +513,79 @@ __global__ void __launch_bounds__(T) k_stockham_small(const float2* in, float2* 
     }
 }
 
+// Row pitch (complex) of the staged tile: an odd number of 16-byte units per
+// row, so that the 16-byte row accesses of a warp spread over all banks
+// (N + 2 when that is odd in 16-byte units, else N + 4: at N = 14 a pitch of
+// 16 complex put every row on the same banks and ran at half the rate).
+constexpr int small2_pitch(int n) { return ((n + 2) / 2) % 2 == 1 ? n + 2 : n + 4; }
+
+// One row per thread for a length N = R1 * R2 (a mixed-radix length too long
+// for one codelet, N <= 56): the tile is staged through shared memory as in
+// k_stockham_small, and each thread runs both Stockham stages of its row in
+// registers.  Stage 1 (radix R1, L = 1): butterfly b < R2 takes x[b + q*R2]
+// and writes y[b*R1 + q]; stage 2 (radix R2, L = R1): butterfly k < R1 takes
+// y[k + q*R1] * w_N^(q*k) from the plan's stage block W[(q-1)*R1 + k] and
+// writes the output element q*R1 + k (natural order).
+template <int N, int S, int T, int R1, int R2>
+__global__ void __launch_bounds__(T) k_stockham_small2(const float2* in, float2* out, const float2* __restrict__ tw,
+                                                        long long batch) {
+    static_assert(N == R1 * R2 && N % 2 == 0, "staged rows need an even length R1 * R2");
+    constexpr int P = small2_pitch(N);
+    extern __shared__ float2 sm[];
+    const long long tile = blockIdx.x;
+    const int nvalid = tile_rows(tile, T, batch);
+    const int tid = threadIdx.x;
+    const float4* g4 = reinterpret_cast<const float4*>(in + tile * T * N);
+    float4* o4 = reinterpret_cast<float4*>(out + tile * T * N);
+    const int nf = nvalid * (N / 2);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const int f = tid + i * T;
+        if (f < nf) {
+            const int row = (2 * f) / N, col = (2 * f) % N;
+            *reinterpret_cast<float4*>(&sm[row * P + col]) = g4[f];
+        }
+    }
+    __syncthreads();
+    float2 v[N];
+#pragma unroll
+    for (int n = 0; n < N; n += 2) {
+        const float4 p = *reinterpret_cast<const float4*>(&sm[tid * P + n]);
+        v[n] = make_float2(p.x, p.y);
+        v[n + 1] = make_float2(p.z, p.w);
+    }
+    float2 y[N];
+#pragma unroll
+    for (int b = 0; b < R2; ++b) {
+        float2 a[R1];
+#pragma unroll
+        for (int q = 0; q < R1; ++q) a[q] = v[b + q * R2];
+        Dft<S, R1>::run(a);
+#pragma unroll
+        for (int q = 0; q < R1; ++q) y[b * R1 + q] = a[q];
+    }
+#pragma unroll
+    for (int k = 0; k < R1; ++k) {
+        float2 a[R2];
+        a[0] = y[k];
+#pragma unroll
+        for (int q = 1; q < R2; ++q) a[q] = k == 0 ? y[k + q * R1] : twiddle<S>(y[k + q * R1], __ldg(&tw[(q - 1) * R1 + k]));
+        Dft<S, R2>::run(a);
+#pragma unroll
+        for (int q = 0; q < R2; ++q) v[q * R1 + k] = a[q];
+    }
+#pragma unroll
+    for (int n = 0; n < N; n += 2)
+        *reinterpret_cast<float4*>(&sm[tid * P + n]) = make_float4(v[n].x, v[n].y, v[n + 1].x, v[n + 1].y);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const int f = tid + i * T;
+        if (f < nf) {
+            const int row = (2 * f) / N, col = (2 * f) % N;
+            o4[f] = *reinterpret_cast<const float4*>(&sm[row * P + col]);
+        }
+    }
+}
+
 }  // namespace gbfft

@@ -104,8 +104,25 @@ inline RowsVariant make_small_variant() {
                        (const void*)&k_stockham_small<N, +1, T>};
 }
 
+// One row per thread, two register-resident Stockham stages (N = R1 * R2).
+template <int N, int T, int R1, int R2>
+inline RowsVariant make_small2_variant() {
+    return RowsVariant{kRowsSmall,
+                       N,
+                       N,
+                       T,
+                       T,
+                       0,
+                       2,
+                       {R1, R2},
+                       (int)(T * small2_pitch(N) * sizeof(float2)),
+                       (const void*)&k_stockham_small2<N, -1, T, R1, R2>,
+                       (const void*)&k_stockham_small2<N, +1, T, R1, R2>};
+}
+
 }  // namespace gbfft
 
+#define GBFFT_SMALL2(N, T, R1, R2) ::gbfft::make_small2_variant<N, T, R1, R2>()
 #define GBFFT_ROWS(N, E, T, PS, ...) ::gbfft::make_rows_variant<N, E, T, PS, __VA_ARGS__>()
 #define GBFFT_ROWS_PF(N, E, T, PS, ...) ::gbfft::make_rows_pf_variant<N, E, T, PS, __VA_ARGS__>()
 #define GBFFT_SMALL(N, T) ::gbfft::make_small_variant<N, T>()
