@@ -431,9 +431,12 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds);
  * with no copies and no arena bytes for its rows; otherwise its rows are
  * copied into the slot, transformed there and copied back.  Input and output
  * must then not overlap partially (the same buffer is fine).  The other
- * lengths are grouped by
- * (n, direction) into one slot and one launch each.  Each group runs on the
- * next stream of the pool: requests arriving while earlier groups run are
+ * lengths (and every length with GBFFT_SERVER_PER_LENGTH) are grouped by
+ * (n, direction): device-visible, 16-byte aligned requests are transformed
+ * where they are (the group's slot holds only a two-pass workspace), others
+ * are copied into one slot and transformed there by one launch.  Each group
+ * runs on the stream with the fewest bytes in flight: requests arriving
+ * while earlier groups run are
  * admitted as memory frees up and overlap them.  Schedules, ragged length
  * descriptors and twiddle tables are built once per length and stay resident
  * (gbfft_server_prepare builds them ahead).  An event recorded after each

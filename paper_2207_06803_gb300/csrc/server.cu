@@ -342,12 +342,44 @@ bool launch_ragged_group(Server* s, Group* g) {
 
 // Launch one group: H2D of each request into the slot, one transform over
 // all rows (in place), D2H of each request, completion stamp.
+// A request a per-length group can transform where its buffers are: both
+// device-visible and 16-byte aligned (the row kernels move 16-byte units).
+bool direct_single(const Server* s, const Request* r) {
+    return s->direct_io && !s->serial && r->din && ((uintptr_t)r->din & 15u) == 0 && ((uintptr_t)r->dout & 15u) == 0;
+}
+
+// Arena bytes a request's group needs: its rows (staged) or only the two-pass
+// workspace (direct).
+size_t group_bytes(const Server* s, int64_t n, int64_t rows, bool two_pass, bool direct) {
+    (void)s;
+    if (!direct) return slot_bytes(n, rows, two_pass);
+    return two_pass ? ((sizeof(float2) * (size_t)n * (size_t)rows + 255) & ~size_t(255)) : 256;
+}
+
 bool launch_group(Server* s, Group* g, ServerPlan* sp, int64_t n, int dir, int64_t rows) {
     float2* data = (float2*)(s->arena_base + g->off);
     const size_t row_bytes = sizeof(float2) * (size_t)n;
     bool ok = true;
     size_t at = 0;
     record_phase(s, g, 0);
+    if (g->direct) {  // each request transformed where it is; the slot holds the two-pass workspace only
+        record_phase(s, g, 1);
+        for (Request* r : g->reqs) {
+            const float2* din = (const float2*)r->din;
+            float2* dout = (float2*)r->dout;
+            if (!sp->two_pass) {
+                ok = ok && launch_rows(*sp->rv, dir, din, dout, sp->tw, (long long)r->batch, sp->grid_cap, g->stream,
+                                       s->status) == cudaSuccess;
+            } else {
+                ok = ok && launch_cols(*sp->cm, 1, dir, din, data, sp->tw_m, sp->post, (long long)r->batch,
+                                       (int)sp->k, g->stream) == cudaSuccess;
+                ok = ok && launch_cols(*sp->ck, 2, dir, data, dout, sp->tw_k, nullptr, (long long)r->batch,
+                                       (int)sp->m, g->stream) == cudaSuccess;
+            }
+        }
+        record_phase(s, g, 2);
+        return ok && cudaEventRecord(g->ev, g->stream) == cudaSuccess;
+    }
     for (Request* r : g->reqs) {
         ok = ok && cudaMemcpyAsync((char*)data + at, r->in, row_bytes * (size_t)r->batch, cudaMemcpyDefault,
                                    g->stream) == cudaSuccess;
@@ -484,7 +516,7 @@ void worker_main(Server* s) {
             const bool rg = can_ragged(s, r);
             const bool direct = rg && s->direct_io && r->din;
             const size_t need = rg ? (direct ? 0 : ragged_share(r)) + 40 * (size_t)r->batch + 512
-                                   : slot_bytes(r->n, r->batch, needs_two_pass(r->n)) + 256;
+                                   : group_bytes(s, r->n, r->batch, needs_two_pass(r->n), direct_single(s, r)) + 256;
             if (s->arena->used() + pending_bytes + need > s->arena->size()) break;
             s->queue.pop_front();
             admitted.push_back(r);
@@ -565,7 +597,9 @@ void worker_main(Server* s) {
             auto g = std::make_unique<Group>();
             g->reqs = std::move(reqs);
             g->direction = dir;
-            g->bytes = slot_bytes(n, rows, sp->two_pass);
+            g->direct = true;
+            for (Request* r : g->reqs) g->direct = g->direct && direct_single(s, r);
+            g->bytes = group_bytes(s, n, rows, sp->two_pass, g->direct);
             return start(std::move(g), [&](Group* gg) { return launch_group(s, gg, sp, n, dir, rows); });
         };
         auto start_ragged = [&](std::vector<Request*> reqs, int dir, bool direct) -> int {  // 1 started, 0 no slot,
