@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <iterator>
 #include <map>
 #include <new>
 #include <vector>
@@ -187,6 +188,24 @@ static gbfft_status ragged_build_items(RaggedState* r) {
                 return cls_cost[a.cls] > cls_cost[b.cls] || (cls_cost[a.cls] == cls_cost[b.cls] && a.cls > b.cls);
             return a.cost > b.cost;
         });
+    }
+    // The last wave of the queue: items of many rows are halved, so that CTAs finish close together.
+    {
+        std::vector<Pending> tail;
+        const size_t k = std::min(pend.size(), (size_t)std::max(r->grid, 1));
+        for (size_t i = pend.size() - k; i < pend.size(); ++i) {
+            Pending& p = pend[i];
+            if (p.rows.size() >= 2) {
+                const size_t h = p.rows.size() / 2;
+                Pending q;
+                q.cls = p.cls;
+                q.rows.assign(p.rows.begin() + (std::ptrdiff_t)h, p.rows.end());
+                p.rows.resize(h);
+                q.cost = p.cost = p.cost / 2;
+                tail.push_back(std::move(q));
+            }
+        }
+        pend.insert(pend.end(), std::make_move_iterator(tail.begin()), std::make_move_iterator(tail.end()));
     }
     for (const Pending& p : pend) {
         RaggedItem it{};

@@ -302,10 +302,11 @@ __device__ __forceinline__ void ragged_cp_async8(void* dst, const void* src) {
 __device__ __forceinline__ void ragged_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Queue entries are claimed by thread 0 in chunks of kRaggedChunk consecutive
-// entries (one atomic per chunk, issued a chunk ahead).  Consecutive entries
-// mostly share a length, so a CTA tends to run the same compiled schedule
-// several times in a row (its instructions stay cached).
-constexpr int kRaggedChunk = 2;
+// entries (one atomic per chunk, issued a chunk ahead).  Chunks of two
+// (consecutive entries mostly share a length) measured the same on the
+// 10,000-transform mix and strand CTAs on short queues: every CTA books two
+// chunks at its start, so 248 single-item entries ran on 124 CTAs.
+constexpr int kRaggedChunk = 1;
 
 // The persistent kernel.  The queue's latencies are taken off the path between
 // items: during item i, thread 0 claims the entry of item i+2 and copies it
