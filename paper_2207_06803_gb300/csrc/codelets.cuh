@@ -1,4 +1,4 @@
-// Register codelets: DFT_r for r in {2, 3, 4, 5, 7, 8, 16, 32, 64}, fully unrolled, on
+// Register codelets: DFT_r for r in {2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64}, fully unrolled, on
 // float2 (FP32 path) or double2 (FP64 path) values.
 //
 // Each codelet computes A = DFT_r a in place on r complex values held in
@@ -8,7 +8,8 @@
 // GPU counterpart of the small solved sub-problems a DFT planner bottoms out in
 // (Sec. III).  Composite codelets use the split of Eq. 2 internally
 // (DFT_8 = 2 x 4, DFT_16 = 4 x 4, DFT_32 = 2 x 16, DFT_64 = 8 x 8); the odd primes use the symmetric
-// sum/difference form of the direct DFT.
+// sum/difference form of the direct DFT; the products of an odd prime and a power of two
+// (6, 10, 12, 14, 20, 24, 28, 40, 48, 56) use the prime-factor map, which needs no twiddles.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -343,5 +344,68 @@ template <int S>
 struct Dft<S, 5> : DftPrime<S, 5> {};
 template <int S>
 struct Dft<S, 7> : DftPrime<S, 7> {};
+
+// x^-1 mod m for coprime x, m (compile time).
+constexpr int inverse_mod(int x, int m) {
+    for (int y = 0; y < m; ++y)
+        if ((x * y) % m == 1 % m) return y;
+    return -1;
+}
+
+// DFT_{P*Q} for coprime P, Q by the prime-factor (Good-Thomas) index maps:
+// input n = (Q*n1 + P*n2) mod PQ, output k with k = k1 (mod P), k = k2 (mod Q)
+// (k = (k1*Q*(Q^-1 mod P) + k2*P*(P^-1 mod Q)) mod PQ, the Chinese remainder
+// map).  Then w_PQ^(nk) = w_P^(n1*k1) * w_Q^(n2*k2), so
+//   A_k = sum_n1 w_P^(n1 k1) sum_n2 w_Q^(n2 k2) a[(Q n1 + P n2) mod PQ]:
+// P DFT_Q over n2, then Q DFT_P over n1, with no twiddle factors between them
+// (unlike the split of Eq. 2, which needs them when the factors share a
+// divisor).  All indices are compile-time constants: the maps cost no
+// instructions.
+template <int S, int P, int Q>
+struct DftPfa {
+    template <class C>
+    __device__ __forceinline__ static void run(C* a) {
+        constexpr int R = P * Q;
+        constexpr int QI = inverse_mod(Q % P, P), PI = inverse_mod(P % Q, Q);
+        static_assert(QI >= 0 && PI >= 0, "P and Q must be coprime");
+        C y[P][Q];
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) {
+#pragma unroll
+            for (int n2 = 0; n2 < Q; ++n2) y[n1][n2] = a[(Q * n1 + P * n2) % R];
+            Dft<S, Q>::run(y[n1]);
+        }
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) {
+            C z[P];
+#pragma unroll
+            for (int n1 = 0; n1 < P; ++n1) z[n1] = y[n1][k2];
+            Dft<S, P>::run(z);
+#pragma unroll
+            for (int k1 = 0; k1 < P; ++k1) a[(k1 * Q * QI + k2 * P * PI) % R] = z[k1];
+        }
+    }
+};
+
+template <int S>
+struct Dft<S, 6> : DftPfa<S, 3, 2> {};
+template <int S>
+struct Dft<S, 10> : DftPfa<S, 5, 2> {};
+template <int S>
+struct Dft<S, 12> : DftPfa<S, 3, 4> {};
+template <int S>
+struct Dft<S, 14> : DftPfa<S, 7, 2> {};
+template <int S>
+struct Dft<S, 20> : DftPfa<S, 5, 4> {};
+template <int S>
+struct Dft<S, 24> : DftPfa<S, 3, 8> {};
+template <int S>
+struct Dft<S, 28> : DftPfa<S, 7, 4> {};
+template <int S>
+struct Dft<S, 40> : DftPfa<S, 5, 8> {};
+template <int S>
+struct Dft<S, 48> : DftPfa<S, 3, 16> {};
+template <int S>
+struct Dft<S, 56> : DftPfa<S, 7, 8> {};
 
 }  // namespace gbfft

@@ -71,6 +71,7 @@ struct RaggedLenState {
     int64_t n = 0;
     std::vector<int64_t> members;               // transform indices of this length
     std::vector<std::vector<int>> cands;        // candidate schedules
+    int runtime_cands = 0;                      // the first runtime_cands run on the run-time engine
     std::vector<int> tw_base;                   // twiddle-table offset of each candidate
     int cand = 0;                               // schedule in use by the run-time engine
     int split = 1;                              // tile shape: rows per item = (rows of the tile) / split
@@ -306,6 +307,7 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
         RaggedLenState& L = r->lens[c];
         L.n = distinct[c];
         L.cands = schedules_of(L.n);
+        L.runtime_cands = (int)L.cands.size();  // a compiled schedule appended below may use composite radices
         L.body = L.n <= kRaggedMaxN ? ragged_body_id((int)L.n) : -1;
         if (L.body >= 0) {  // the compiled schedule's twiddle blocks come with the candidates
             std::vector<int> sch;
@@ -496,7 +498,7 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
         for (int sp : {1, 2, 4, 8})
             if (tile_rows / sp >= 1) trial(&L.split, sp);
         if (!L.use_body)
-            for (int k = 0; k < (int)L.cands.size(); ++k) trial(&L.cand, k);
+            for (int k = 0; k < L.runtime_cands; ++k) trial(&L.cand, k);
     }
     if (st == GBFFT_OK) st = ragged_build_items(r);
     ragged_release_graph(r);

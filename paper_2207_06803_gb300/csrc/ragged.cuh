@@ -77,9 +77,11 @@ static_assert(sizeof(RaggedItem) == 32, "queue entries are copied in two 16-byte
 // engine of stockham.cuh with constant strides, so index arithmetic folds into
 // addressing and the twiddle loop bounds are known.  X(N, T, radices...): T
 // rows per item (T * N <= 8192 elements; for p = 3, 5, 7 the tile is capped so
-// that the radix-p stage holds at most 16 complex per thread), radices in
-// application order (the odd radix first, as in the single-pass variants).
-// Every other 7-smooth length runs the run-time engine.
+// that the first stage holds at most 16 complex per thread where it can),
+// radices in application order.  The first stage carries the odd factor: a
+// lone radix p, or a composite p * 2^j (DFT_6 ... DFT_28, prime-factor
+// codelets) where that saves a fourth stage or an uneven radix-2/4 stage.
+// Every other 7-smooth length runs the run-time engine (radices 2 ... 16).
 #define GBFFT_RAGGED_BODIES(X)   \
     X(8, 512, 2, 4)              \
     X(16, 512, 4, 4)             \
@@ -95,32 +97,32 @@ static_assert(sizeof(RaggedItem) == 32, "queue entries are copied in two 16-byte
     X(12, 512, 3, 4)             \
     X(24, 320, 3, 8)             \
     X(48, 160, 3, 16)            \
-    X(96, 80, 3, 2, 16)          \
-    X(192, 40, 3, 4, 16)         \
+    X(96, 64, 6, 16)             \
+    X(192, 32, 12, 16)           \
     X(384, 20, 3, 8, 16)         \
     X(768, 10, 3, 16, 16)        \
-    X(1536, 5, 3, 16, 16, 2)     \
-    X(3072, 2, 3, 16, 16, 4)     \
+    X(1536, 4, 6, 16, 16)        \
+    X(3072, 2, 12, 16, 16)       \
     X(6144, 1, 3, 16, 16, 8)     \
     X(10, 512, 5, 2)             \
     X(20, 384, 5, 4)             \
     X(40, 192, 5, 8)             \
     X(80, 96, 5, 16)             \
-    X(160, 48, 5, 2, 16)         \
+    X(160, 32, 10, 16)           \
     X(320, 24, 5, 4, 16)         \
     X(640, 12, 5, 8, 16)         \
     X(1280, 6, 5, 16, 16)        \
-    X(2560, 3, 5, 16, 16, 2)     \
+    X(2560, 2, 10, 16, 16)       \
     X(5120, 1, 5, 16, 16, 4)     \
     X(14, 512, 7, 2)             \
     X(28, 256, 7, 4)             \
     X(56, 128, 7, 8)             \
     X(112, 64, 7, 16)            \
-    X(224, 32, 7, 2, 16)         \
+    X(224, 32, 14, 16)           \
     X(448, 16, 7, 4, 16)         \
     X(896, 8, 7, 8, 16)          \
     X(1792, 4, 7, 16, 16)        \
-    X(3584, 2, 7, 16, 16, 2)     \
+    X(3584, 2, 14, 16, 16)       \
     X(7168, 1, 7, 16, 16, 4)
 
 // Host-side description of a compiled schedule (plan building, autotuner).
