@@ -76,7 +76,7 @@ def test_variant_registry_is_consistent(lib):
             info = gbfft.gbfft_variant_info(n, i)
             prod = 1
             for r in info["radices"]:
-                assert r in (2, 3, 4, 5, 7, 8, 16, 32, 64)
+                assert r in (2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 28, 32, 40, 48, 56, 64)
                 prod *= r
             assert prod == n
             assert info["threads_per_cta"] * (n * info["rows_per_cta"] // info["threads_per_cta"]) \
