@@ -343,7 +343,7 @@ gbfft_status gbfft_plan_ragged(gbfft_plan *out, const int64_t *n, const int64_t 
 gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void *cuda_stream);
 
 /*
- * Autotuner for a ragged plan: tries both queue orders, then for each length,
+ * Autotuner for a ragged plan: tries the three queue orders, then for each length,
  * heaviest first, the compiled or the run-time engine (gbfft_ragged_set_engine),
  * the tile split 1, 2, 4, 8 (rows per item = (rows of the engine's tile)/split),
  * and, on the run-time engine, each candidate radix schedule of the length,
@@ -354,9 +354,16 @@ gbfft_status gbfft_execute_ragged(gbfft_plan p, const void *in, void *out, void 
  */
 gbfft_status gbfft_ragged_autotune(gbfft_plan p, const void *in, void *out, int reps, float *best_ms);
 
-/* Queue order the plan uses (-1 if not a ragged plan): 1 (default) keeps the
- * items of one length together, heaviest length first; 0 orders all items by
- * work, heaviest first.  The autotuner tries both. */
+/* Queue order of a ragged plan.  0: one queue, all items by work, heaviest
+ * first.  1 (default): one queue, the items of one length together, heaviest
+ * length first.  2: one sub-queue per length (in the order of 1), each SM
+ * starting on a home sub-queue (SMs dealt to lengths in proportion to their
+ * elements) and moving on to the next sub-queue when its own is exhausted, so
+ * that an SM runs few distinct lengths.  Every order computes the same
+ * results.  gbfft_ragged_set_queue_order sets it and rebuilds the queue
+ * (INVALID_ARG for another value or plan kind); gbfft_ragged_queue_order
+ * returns it (-1 if not a ragged plan).  The autotuner tries all three. */
+gbfft_status gbfft_ragged_set_queue_order(gbfft_plan p, int order);
 int gbfft_ragged_queue_order(gbfft_plan p);
 
 /* Radix schedule the plan uses for length n: its stage count (0 if n is not in

@@ -850,6 +850,11 @@ gbfft_status gbfft_ragged_set_wait_limit(gbfft_plan p, int64_t nanoseconds) {
     return GBFFT_OK;
 }
 
+gbfft_status gbfft_ragged_set_queue_order(gbfft_plan p, int order) {
+    if (!p || p->kind != kPlanRagged || order < 0 || order > 2) return GBFFT_ERR_INVALID_ARG;
+    return ragged_set_queue_order(p->ragged, order);
+}
+
 int gbfft_ragged_queue_order(gbfft_plan p) {
     if (!p || p->kind != kPlanRagged) return -1;
     return ragged_queue_order(p->ragged);

@@ -175,23 +175,36 @@ RowsVariant make_cluster_variant() {
 
 #define GBFFT_CLUSTER(N, K, TPB, PS, VA, ...) make_cluster_variant<N, K, TPB, PS, VA, __VA_ARGS__>()
 
-// Column schedules are the single-pass ones of the same lengths; the radix
-// list of a variant is the column schedule followed by K.  The grouped phase A
-// (VA) measured faster everywhere but on N = 8192 and 16384 with K = 2, whose
-// kernels spill with it (8192: 3.31 against 3.57 TB/s).
+// The radix list of a variant is the column schedule followed by K.  The
+// first entry of each length is its cluster default: a CTA pair whose column
+// schedule opens with a composite p * 2^j stage (three stages: the
+// single-pass schedules of those lengths) where the length has an odd factor;
+// the radix-p-first schedules (four stages) and wider clusters follow as
+// alternatives.  The grouped phase A (VA) measured faster everywhere but on
+// N = 8192 and 16384 with K = 2, whose kernels spill with it (8192: 3.31
+// against 3.57 TB/s).
 const RowsVariant kCluster[] = {
+    GBFFT_CLUSTER(5120, 2, 160, 0, true, 20, 8, 16),
     GBFFT_CLUSTER(5120, 2, 160, 5, true, 5, 16, 16, 2),
+    GBFFT_CLUSTER(6144, 2, 192, 5, true, 24, 8, 16),
     GBFFT_CLUSTER(6144, 2, 192, 4, true, 3, 16, 16, 4),
+    GBFFT_CLUSTER(7168, 2, 256, 0, true, 14, 16, 16),
     GBFFT_CLUSTER(7168, 2, 224, 4, true, 7, 16, 16, 2),
     GBFFT_CLUSTER(8192, 2, 256, 4, false, 16, 16, 16),
     GBFFT_CLUSTER(8192, 4, 128, 4, true, 16, 16, 8),
-    GBFFT_CLUSTER(10240, 2, 320, 4, true, 5, 16, 16, 4),  // CTA pairs on 5120-8192-long columns first: fewer
-    GBFFT_CLUSTER(10240, 4, 160, 5, true, 5, 16, 16, 2),  // CTAs per row measured faster (N = 16384: K = 2 at
-    GBFFT_CLUSTER(12288, 2, 384, 4, true, 3, 16, 16, 8),  // 0.87x the two passes, K = 4 at 0.63x)
+    GBFFT_CLUSTER(10240, 2, 320, 0, true, 20, 16, 16),  // CTA pairs on 5120-8192-long columns first: fewer
+    GBFFT_CLUSTER(10240, 2, 320, 4, true, 5, 16, 16, 4),  // CTAs per row measured faster (N = 16384: K = 2 at
+    GBFFT_CLUSTER(10240, 4, 160, 5, true, 5, 16, 16, 2),  // 0.86x the two passes, K = 4 at 0.80x)
+    GBFFT_CLUSTER(12288, 2, 384, 0, true, 24, 16, 16),
+    GBFFT_CLUSTER(12288, 2, 384, 4, true, 3, 16, 16, 8),
+    GBFFT_CLUSTER(12288, 4, 192, 5, true, 24, 8, 16),
     GBFFT_CLUSTER(12288, 4, 192, 4, true, 3, 16, 16, 4),
+    GBFFT_CLUSTER(14336, 2, 448, 0, true, 28, 16, 16),
     GBFFT_CLUSTER(14336, 2, 448, 4, true, 7, 16, 16, 4),
+    GBFFT_CLUSTER(14336, 4, 256, 0, false, 14, 16, 16),
     GBFFT_CLUSTER(14336, 4, 224, 4, true, 7, 16, 16, 2),
     GBFFT_CLUSTER(16384, 2, 512, 4, false, 16, 16, 16, 2),
+    GBFFT_CLUSTER(16384, 2, 512, 4, false, 32, 16, 16),
     GBFFT_CLUSTER(16384, 4, 256, 4, true, 16, 16, 16),
     GBFFT_CLUSTER(16384, 8, 128, 4, true, 16, 16, 8),
     GBFFT_CLUSTER(20480, 4, 320, 4, true, 5, 16, 16, 4),
@@ -207,9 +220,10 @@ const RowsVariant kCluster[] = {
 }  // namespace
 
 // Lengths whose default plan is the cluster kernel (variant 0) rather than Eq. 2 as two passes:
-// where it measured faster on GB300.  N = 8192 on a pair of CTAs: 1.07x the two passes; the other
-// K = 2 lengths 0.90-0.98x, K = 4 and 8 at most 0.76x.
-bool cluster_is_default(int64_t n) { return n == 8192; }
+// where it measured faster on GB300 (2^26 points): on a CTA pair, 5120 1.18x the two passes, 6144
+// 1.11x, 7168 1.08x, 8192 1.06x, 10240 1.07x.  At 12288 / 14336 / 16384 the best cluster variants
+// reach 0.95x / 1.01x / 0.86x (384-512-thread CTAs, two per SM), so the two passes stay the default.
+bool cluster_is_default(int64_t n) { return n == 5120 || n == 6144 || n == 7168 || n == 8192 || n == 10240; }
 
 int cluster_variants_for(int64_t n, const RowsVariant** out, int max_out) {
     int found = 0;

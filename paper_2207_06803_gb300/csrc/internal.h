@@ -123,6 +123,7 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
                              float* best_ms);
 int ragged_class_split(const RaggedState* r, int64_t n);
 int ragged_queue_order(const RaggedState* r);
+gbfft_status ragged_set_queue_order(RaggedState* r, int order);
 gbfft_status ragged_set_engine(RaggedState* r, int64_t n, int compiled);
 int ragged_engine(const RaggedState* r, int64_t n);
 

@@ -85,14 +85,17 @@ struct RaggedState {
     int64_t total = 0;  // elements spanned by the transforms (max offset + n)
     std::vector<int64_t> n, off;
     std::vector<RaggedLenState> lens;           // one per distinct length
-    int order = 1;                              // queue order: 0 = heaviest item first, 1 = grouped by length
+    int order = 1;                              // queue order: 0 = heaviest item first, 1 = grouped by length,
+                                                // 2 = one sub-queue per length, home sub-queues spread over the SMs
     std::vector<RaggedItem> items;
     std::vector<long long> row_offs;
     RaggedItem* d_items = nullptr;
     long long* d_offs = nullptr;
     RaggedLen* d_lens = nullptr;
     float2* d_tw = nullptr;
-    int* d_counter = nullptr;
+    int* d_counter = nullptr;                   // one claim counter per sub-queue
+    int* d_qtab = nullptr;                      // queue table (k_ragged's qtab)
+    std::vector<int> qtab;
     int grid = 0;
     long long wait_ns = 200000000LL;  // 200 ms bound on any ready-wait
     cudaGraph_t graph = nullptr;
@@ -118,6 +121,7 @@ void ragged_destroy(RaggedState* r) {
     if (r->d_lens) cudaFree(r->d_lens);
     if (r->d_tw) cudaFree(r->d_tw);
     if (r->d_counter) cudaFree(r->d_counter);
+    if (r->d_qtab) cudaFree(r->d_qtab);
     delete r;
 }
 
@@ -181,7 +185,7 @@ static gbfft_status ragged_build_items(RaggedState* r) {
     }
     if (r->order == 0) {
         std::stable_sort(pend.begin(), pend.end(), [](const Pending& a, const Pending& b) { return a.cost > b.cost; });
-    } else {
+    } else {  // 1 and 2: grouped by length
         std::vector<double> cls_cost(nl, 0.0);
         for (const Pending& p : pend) cls_cost[p.cls] = std::max(cls_cost[p.cls], p.cost);
         std::stable_sort(pend.begin(), pend.end(), [&](const Pending& a, const Pending& b) {
@@ -191,7 +195,7 @@ static gbfft_status ragged_build_items(RaggedState* r) {
         });
     }
     // The last wave of the queue: items of many rows are halved, so that CTAs finish close together.
-    {
+    if (r->order != 2) {
         std::vector<Pending> tail;
         const size_t k = std::min(pend.size(), (size_t)std::max(r->grid, 1));
         for (size_t i = pend.size() - k; i < pend.size(); ++i) {
@@ -217,8 +221,58 @@ static gbfft_status ragged_build_items(RaggedState* r) {
         r->items.push_back(it);
         r->row_offs.insert(r->row_offs.end(), p.rows.begin(), p.rows.end());
     }
+    // Queue table: one shared queue (orders 0, 1), or one sub-queue per length in queue order (2) with
+    // each SM's home sub-queue: SMs are dealt to the sub-queues in proportion to their elements (largest
+    // remainder), consecutive SM ids to one sub-queue; a sub-queue too small for an SM of its own is
+    // left to the CTAs that finish theirs.
+    r->qtab.clear();
+    if (r->order != 2 || pend.empty()) {
+        r->qtab = {1, 0, 0, (int)pend.size()};
+    } else {
+        std::vector<int> start;
+        std::vector<double> work;
+        for (size_t i = 0; i < pend.size(); ++i) {
+            if (i == 0 || pend[i].cls != pend[i - 1].cls) {
+                start.push_back((int)i);
+                work.push_back(0.0);
+            }
+            work.back() += (double)pend[i].rows.size() * (double)r->lens[pend[i].cls].n;
+        }
+        const int nq = (int)start.size();
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+            nsm = 1;
+        double total = 0.0;
+        for (double w : work) total += w;
+        std::vector<int> sms(nq, 0);
+        std::vector<std::pair<double, int>> rem;
+        int dealt = 0;
+        for (int k = 0; k < nq; ++k) {
+            const double share = work[k] / total * nsm;
+            sms[k] = (int)share;
+            dealt += sms[k];
+            rem.push_back({share - sms[k], k});
+        }
+        std::stable_sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+        for (size_t i = 0; dealt < nsm && i < rem.size(); ++i, ++dealt) ++sms[rem[i].second];
+        r->qtab.push_back(nq);
+        r->qtab.push_back(nsm);
+        for (int k = 0; k < nq; ++k) r->qtab.push_back(start[k]);
+        r->qtab.push_back((int)pend.size());
+        for (int k = 0; k < nq; ++k)
+            for (int i = 0; i < sms[k]; ++i) r->qtab.push_back(k);
+    }
     std::vector<RaggedLen> desc(nl);
     for (int c = 0; c < nl; ++c) desc[c] = describe(r->lens[c]);
+    if (r->d_qtab) cudaFree(r->d_qtab);
+    r->d_qtab = nullptr;
+    if (cudaMalloc(&r->d_qtab, sizeof(int) * r->qtab.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return GBFFT_ERR_OOM;
+    }
+    if (cudaMemcpy(r->d_qtab, r->qtab.data(), sizeof(int) * r->qtab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return GBFFT_ERR_CUDA;
     if (r->d_items) cudaFree(r->d_items);
     if (r->d_offs) cudaFree(r->d_offs);
     r->d_items = nullptr;
@@ -246,18 +300,19 @@ static void ragged_args(RaggedState* r, const float2** pin, float2** pout, int* 
     args[5] = (void*)&r->d_lens;
     args[6] = (void*)&r->d_tw;
     args[7] = (void*)&r->d_counter;
-    args[8] = (void*)status;
-    args[9] = (void*)&r->wait_ns;
+    args[8] = (void*)&r->d_qtab;
+    args[9] = (void*)status;
+    args[10] = (void*)&r->wait_ns;
 }
 
 static cudaError_t ragged_launch(RaggedState* r, int direction, const void* in, void* out, int* status,
                                  cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(r->d_counter, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(r->d_counter, 0, sizeof(int) * (size_t)r->qtab[0], s);
     if (e != cudaSuccess) return e;
     int nitems = (int)r->items.size();
     const float2* pin = (const float2*)in;
     float2* pout = (float2*)out;
-    void* args[10];
+    void* args[11];
     ragged_args(r, &pin, &pout, &nitems, &status, args);
     const void* fn = direction == GBFFT_FORWARD ? ragged_kernel_fwd() : ragged_kernel_inv();
     const int grid = std::min<int>(r->grid, nitems > 0 ? nitems : 1);
@@ -331,7 +386,7 @@ gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* o
     gbfft_status st = GBFFT_OK;
     if (cudaMalloc(&r->d_tw, sizeof(float2) * (size_t)std::max(tw_total, 1)) != cudaSuccess ||
         cudaMalloc(&r->d_lens, sizeof(RaggedLen) * r->lens.size()) != cudaSuccess ||
-        cudaMalloc(&r->d_counter, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&r->d_counter, sizeof(int) * std::max<size_t>(distinct.size(), 1)) != cudaSuccess) {
         cudaGetLastError();
         st = GBFFT_ERR_OOM;
     }
@@ -410,7 +465,7 @@ gbfft_status ragged_execute(RaggedState* r, int direction, const void* in, void*
         const float2* pin = (const float2*)in;
         float2* pout = (float2*)out;
         int nitems = (int)r->items.size();
-        void* args[10];
+        void* args[11];
         ragged_args(r, &pin, &pout, &nitems, &status, args);
         kp.kernelParams = args;
         if (cudaGraphExecKernelNodeSetParams(r->exec, r->knode, &kp) != cudaSuccess ||
@@ -485,7 +540,7 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
         if (st == GBFFT_OK && ms < best) best = ms;
         else *knob = keep;
     };
-    trial(&r->order, 1 - r->order);
+    for (int o : {0, 1, 2}) trial(&r->order, o);
     std::vector<int> order;
     for (int c = 0; c < (int)r->lens.size(); ++c) order.push_back(c);
     std::sort(order.begin(), order.end(), [&](int a, int b) {
@@ -511,6 +566,12 @@ gbfft_status ragged_autotune(RaggedState* r, int direction, const void* in, void
 }
 
 int ragged_queue_order(const RaggedState* r) { return r->order; }
+
+gbfft_status ragged_set_queue_order(RaggedState* r, int order) {
+    r->order = order;
+    ragged_release_graph(r);
+    return ragged_build_items(r);
+}
 
 gbfft_status ragged_set_engine(RaggedState* r, int64_t n, int compiled) {
     bool found = false;
@@ -662,13 +723,19 @@ gbfft_status ragged_table_add(RaggedTable* t, int64_t n, cudaStream_t s, int* cl
     return GBFFT_OK;
 }
 
+// A queue blob starts with a 32-byte header: the claim counter (int 0) and a
+// one-queue table (ints 1-4: nq = 1, no home map, the queue spanning entries
+// [0, nitems)), then the entries, then the row offsets.
+constexpr size_t kBlobHeader = 32;
+
 size_t ragged_blob_bytes(int64_t nitems, int64_t nrows) {
-    return 16 + sizeof(RaggedItem) * (size_t)nitems + sizeof(long long) * (size_t)nrows;
+    return kBlobHeader + sizeof(RaggedItem) * (size_t)nitems + sizeof(long long) * (size_t)nrows;
 }
 
 // Queue entries for `nspans` spans of consecutive rows (every span's length
 // already in the table), heaviest entry first, packed into `blob` (at most
-// `cap` bytes): a zero counter, the entries, the row offsets.  Returns the
+// `cap` bytes): the header (a zero counter and the queue table), the entries,
+// the row offsets.  Returns the
 // entry count, or -1 if the blob would not fit.
 int64_t ragged_table_build(const RaggedTable* t, const RaggedSpan* spans, int64_t nspans, char* blob, size_t cap,
                            size_t* bytes) {
@@ -695,10 +762,11 @@ int64_t ragged_table_build(const RaggedTable* t, const RaggedSpan* spans, int64_
     std::vector<size_t> order(items.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-    std::memset(blob, 0, 16);
-    RaggedItem* bi = reinterpret_cast<RaggedItem*>(blob + 16);
+    const int head[kBlobHeader / sizeof(int)] = {0, 1, 0, 0, (int)items.size(), 0, 0, 0};
+    std::memcpy(blob, head, kBlobHeader);
+    RaggedItem* bi = reinterpret_cast<RaggedItem*>(blob + kBlobHeader);
     for (size_t i = 0; i < order.size(); ++i) bi[i] = items[order[i]];
-    long long* bo = reinterpret_cast<long long*>(blob + 16 + sizeof(RaggedItem) * items.size());
+    long long* bo = reinterpret_cast<long long*>(blob + kBlobHeader + sizeof(RaggedItem) * items.size());
     for (int64_t k = 0, row = 0; k < nspans; ++k)
         for (int64_t r = 0; r < spans[k].rows; ++r) bo[row++] = spans[k].off + r * spans[k].n;
     *bytes = need;
@@ -712,15 +780,17 @@ cudaError_t ragged_table_launch(const RaggedTable* t, int direction, float2* dat
     if (nitems <= 0) return cudaSuccess;
     const float2* pin = data;
     float2* pout = data;
-    const RaggedItem* items = reinterpret_cast<const RaggedItem*>(d_blob + 16);
+    const RaggedItem* items = reinterpret_cast<const RaggedItem*>(d_blob + kBlobHeader);
     int n_items = (int)nitems;
-    const long long* offs = reinterpret_cast<const long long*>(d_blob + 16 + sizeof(RaggedItem) * (size_t)nitems);
+    const long long* offs =
+        reinterpret_cast<const long long*>(d_blob + kBlobHeader + sizeof(RaggedItem) * (size_t)nitems);
     const RaggedLen* lens = t->d_lens;
     const float2* tw = t->d_tw;
     int* counter = reinterpret_cast<int*>(const_cast<char*>(d_blob));
+    const int* qtab = reinterpret_cast<const int*>(d_blob) + 1;
     long long wait_ns = kTableWaitNs;
-    void* args[10] = {(void*)&pin, (void*)&pout, (void*)&items, (void*)&n_items, (void*)&offs,
-                      (void*)&lens, (void*)&tw,  (void*)&counter, (void*)&status, (void*)&wait_ns};
+    void* args[11] = {(void*)&pin, (void*)&pout, (void*)&items,  (void*)&n_items, (void*)&offs,   (void*)&lens,
+                      (void*)&tw,  (void*)&counter, (void*)&qtab, (void*)&status, (void*)&wait_ns};
     const void* fn = direction == GBFFT_FORWARD ? ragged_kernel_fwd() : ragged_kernel_inv();
     const int grid = (int)std::min<int64_t>(t->grid, nitems);
     return cudaLaunchKernel(fn, dim3(grid), dim3(kRaggedThreads), args, (size_t)kRaggedSmemBytes, s);

@@ -1,13 +1,13 @@
 // Ragged batches: thousands of transforms of uneven lengths in one persistent launch.
 //
 // The host groups the transforms by length, gives each length a radix schedule
-// (a Stockham factorisation n = R_1 ... R_t over the radices 2, 3, 4, 5, 7, 8,
-// 16), cuts each group into work items of at most T rows (T * n <= 8192
-// complex elements), orders the items and uploads them with the list of row
-// offsets and one descriptor per length.  Each CTA of the persistent kernel
-// repeatedly claims queue items (in chunks of consecutive items, one atomic
-// per chunk) and runs each item's schedule: the first stage reads the rows
-// straight from HBM, stages exchange through a shared-memory tile, the last
+// (a Stockham factorisation n = R_1 ... R_t), cuts each group into work items
+// of at most T rows (T * n <= 8192 complex elements), orders the items and
+// uploads them with the list of row offsets and one descriptor per length.
+// Each CTA of the persistent kernel repeatedly claims queue items (one atomic
+// per item, from a shared queue or from per-length sub-queues with a home
+// sub-queue per SM) and runs each item's schedule: the first stage reads the
+// rows straight from HBM, stages exchange through a shared-memory tile, the last
 // stage writes straight to HBM (the stage algebra of the single-pass kernel,
 // Eq. 2).  Two engines run a schedule:
 //   compiled  for n = p * 2^k (p = 1, 3, 5, 7, 8 <= n <= 8192): the schedule
@@ -303,25 +303,24 @@ __device__ __forceinline__ void ragged_cp_async8(void* dst, const void* src) {
 }
 __device__ __forceinline__ void ragged_cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Queue entries are claimed by thread 0 in chunks of kRaggedChunk consecutive
-// entries (one atomic per chunk, issued a chunk ahead).  Chunks of two
-// (consecutive entries mostly share a length) measured the same on the
-// 10,000-transform mix and strand CTAs on short queues: every CTA books two
-// chunks at its start, so 248 single-item entries ran on 124 CTAs.
-constexpr int kRaggedChunk = 1;
-
-// The persistent kernel.  The queue's latencies are taken off the path between
-// items: during item i, thread 0 claims the entry of item i+2 and copies it
-// into shared memory (cp.async), and every thread copies the length descriptor
-// and row offsets of item i+1 into the other descriptor slot (cp.async).  One
-// barrier opens each item.  An item then runs its compiled schedule (the
-// single-pass stage engine with the schedule fixed at compile time) or the
-// run-time engine (the schedule read from its descriptor, one stage at a time).
+// The queue is cut into nq sub-queues (consecutive ranges of entries), each
+// with its own claim counter.  Queue table `qtab`: qtab[0] = nq, qtab[1] =
+// nhome, qtab[2 ... 2+nq] = the entry index where each sub-queue starts (the
+// last = nitems), then nhome entries giving the sub-queue each SM (by %smid)
+// starts on.  Thread 0 claims one entry at a time from its current sub-queue
+// and, when that sub-queue is exhausted, moves on to the next one in ring
+// order: sub-queues never refill, so each CTA visits every sub-queue at most
+// once after its home and issues at most nq failing claims in all.  With one
+// sub-queue and no home map this is a single shared queue.  With one
+// sub-queue per length and home sub-queues spread over the SMs in proportion
+// to each length's work, an SM runs few distinct lengths: their compiled code
+// and stage twiddles stay in its caches.
 template <int S>
 __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, float2* out, const RaggedItem* items,
                                                            int nitems, const long long* offs,
                                                            const RaggedLen* __restrict__ lens,
-                                                           const float2* __restrict__ tw, int* counter, int* status,
+                                                           const float2* __restrict__ tw, int* counters,
+                                                           const int* __restrict__ qtab, int* status,
                                                            long long wait_ns) {
     extern __shared__ float2 sm[];
     __shared__ __align__(16) long long s_off[2][kRaggedMaxRows];
@@ -337,20 +336,26 @@ __global__ void __launch_bounds__(kRaggedThreads, 2) k_ragged(const float2* in, 
                               reinterpret_cast<const char*>(lens + d.cls) + 16 * tid);
         for (int t = tid; t < d.count; t += kRaggedThreads) ragged_cp_async8(&s_off[ls][t], offs + d.first + t);
     };
-    int c_pos = 0, c_end = 0, n_pos = 0;  // thread 0: current chunk [c_pos, c_end), start of the next
-    auto claim = [&]() {                   // thread 0: the next queue index
-        const int it = c_pos;
-        if (it < nitems && ++c_pos == c_end) {
-            c_pos = n_pos;
-            c_end = n_pos + kRaggedChunk;
-            n_pos = atomicAdd(counter, kRaggedChunk);
+    int q = 0, nq = 1, left = 0;  // thread 0: current sub-queue, sub-queue count, sub-queues not yet found empty
+    const int* qstart = qtab + 2;
+    auto claim = [&]() {  // thread 0: the next queue index, nitems once every sub-queue is exhausted
+        while (left > 0) {
+            const int idx = qstart[q] + atomicAdd(&counters[q], 1);
+            if (idx < qstart[q + 1]) return idx;
+            q = q + 1 == nq ? 0 : q + 1;
+            --left;
         }
-        return it;
+        return nitems;
     };
     if (tid == 0) {
-        c_pos = atomicAdd(counter, kRaggedChunk);
-        c_end = c_pos + kRaggedChunk;
-        n_pos = atomicAdd(counter, kRaggedChunk);
+        nq = qtab[0];
+        left = nq;
+        const int nhome = qtab[1];
+        if (nhome > 0) {
+            unsigned smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            q = (int)smid < nhome ? qtab[3 + nq + smid] : 0;
+        }
         for (int k = 0; k < 2; ++k) {
             const int id = claim();
             s_id[k] = id;

@@ -79,6 +79,7 @@ PROTOTYPES = {
     "gbfft_ragged_num_items": (_c_i64, [_c_vp]),
     "gbfft_ragged_tile_split": (_c_int, [_c_vp, _c_i64]),
     "gbfft_ragged_queue_order": (_c_int, [_c_vp]),
+    "gbfft_ragged_set_queue_order": (_c_int, [_c_vp, _c_int]),
     "gbfft_ragged_schedule": (_c_int, [_c_vp, _c_i64, _c_intp]),
     "gbfft_ragged_set_engine": (_c_int, [_c_vp, _c_i64, _c_int]),
     "gbfft_ragged_engine": (_c_int, [_c_vp, _c_i64]),
@@ -374,6 +375,10 @@ def gbfft_ragged_set_engine(plan: int, n: int, compiled: int) -> None:
 
 def gbfft_ragged_engine(plan: int, n: int) -> int:
     return int(lib().gbfft_ragged_engine(plan, n))
+
+
+def gbfft_ragged_set_queue_order(plan: int, order: int) -> None:
+    _check(lib().gbfft_ragged_set_queue_order(plan, order), "gbfft_ragged_set_queue_order")
 
 
 def gbfft_ragged_queue_order(plan: int) -> int:

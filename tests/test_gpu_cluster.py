@@ -80,10 +80,12 @@ def test_cluster_full_size_sampled_rows(n):
 
 
 def test_default_plan_above_4096():
-    """The cluster kernel is the default where it measured faster (N = 8192);
-    other lengths above 4096 default to Eq. 2 as two passes."""
+    """The cluster kernel is the default where it measured faster (N = 5120,
+    6144, 7168, 8192, 10240); other lengths above 4096 default to Eq. 2 as two
+    passes."""
     from paper_2207_06803_gb300 import gbfft
-    for n, one_pass in ((8192, True), (5120, False), (16384, False), (65536, False)):
+    for n, one_pass in ((8192, True), (5120, True), (6144, True), (7168, True), (10240, True), (12288, False),
+                        (14336, False), (16384, False), (65536, False)):
         with gbfft.Plan(n, 4, -1) as p:
             k, _ = gbfft.gbfft_plan_factors(p.handle)
             assert (k == 1) == one_pass, (n, k)

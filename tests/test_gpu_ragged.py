@@ -72,6 +72,30 @@ def test_ragged_10000_transforms_41_sizes(direction, engine):
     check_all(y, flat, sizes, offs, direction)
 
 
+def test_ragged_queue_orders_agree():
+    """The three queue orders (one queue by item work; one queue grouped by
+    length; one sub-queue per length with home sub-queues per SM and stealing)
+    only change which CTA runs which item: outputs are bit-identical and match
+    the oracle, and an invalid order is refused."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    sizes, offs, flat = ragged_case(3000, seed=SEED + 5)
+    outs = []
+    with gbfft.RaggedPlan(sizes, offs) as p:
+        assert gbfft.gbfft_ragged_queue_order(p.handle) == 1
+        for order in (0, 1, 2):
+            gbfft.gbfft_ragged_set_queue_order(p.handle, order)
+            assert gbfft.gbfft_ragged_queue_order(p.handle) == order
+            _, d_out = run_plan(p, flat)
+            assert gbfft.gbfft_plan_device_status(p.handle) == 0
+            outs.append(d_out)
+        with pytest.raises(gbfft.GbfftError) as e:
+            gbfft.gbfft_ragged_set_queue_order(p.handle, 3)
+        assert e.value.status == gbfft.GBFFT_ERR_INVALID_ARG
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
+    check_all(to_np(outs[2]), flat, sizes, offs)
+
+
 def test_ragged_in_place_and_buffer_patching():
     import torch
     from paper_2207_06803_gb300 import gbfft
