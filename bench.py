@@ -877,7 +877,7 @@ def run_tc(args, dists=("uniform", "gaussian_scaled")):
         d_in = torch.from_numpy(x[: batch * n].view(np.float32)).cuda()
         d_out = torch.empty_like(d_in)
         d_rt = torch.empty_like(d_in)
-        for name, dt, var in (("fp32", 0, None), ("fp16x2_direct", 1, 2)):
+        for name, dt, var in (("fp32", 0, None), ("fp16x2_direct", 1, 2), ("fp16x2_direct_tile_serial", 1, 3)):
             with gbfft.Plan(n, batch, -1, dt, variant=var) as pf, gbfft.Plan(n, batch, 1, dt, variant=var) as pi:
                 ms = _time_ms(torch, lambda: pf.execute(d_in, d_out, stream), max(5, args.steps // 20), stream)
                 pi.execute(d_out, d_rt, stream)

@@ -98,11 +98,16 @@ int gbfft_version(void);
  * selects the engine: variant 1 (N = 256, 4096; the default there) issues
  * tcgen05.mma from shared-memory operands into tensor memory and reads results
  * back with tcgen05.ld; variant 0 (the default for N = 16) issues warp-level
- * mma.sync.m16n8k16 on register fragments; variant 2 (N = 8, 16, 24, ..., 64;
- * the default except at 16) is the direct DFT: y = F_N x as ONE split-precision
+ * mma.sync.m16n8k16 on register fragments; variants 2 and 3 (N = 8, 16, 24,
+ * ..., 64; FP16x2 only) are the direct DFT: y = F_N x as ONE split-precision
  * real product [yr yi] = [xr xi] [[Fr, Fi], [-Fi, Fr]] per 128 transforms on
  * tcgen05 (M = 128, K = N_out = 2N), no factorisation (the paper's direct-DFT
- * variant, Sec. VI).  The two-pass form is FP32-only (INVALID_ARG otherwise).
+ * variant, Sec. VI).  Variant 2 (the default at N = 24 ... 64) is warp-
+ * specialised: producer warps split rows into tensor memory, one thread issues
+ * the MMAs and epilogue warps read the results back, on consecutive tiles at
+ * once; variant 3 (the default at N = 8) runs each tile's phases one after the
+ * other in every thread of a CTA.  The two-pass form is FP32-only (INVALID_ARG
+ * otherwise).
  */
 gbfft_status gbfft_plan_create(gbfft_plan *out, int64_t n, int64_t batch, int direction, int dtype);
 

@@ -131,7 +131,8 @@ struct gbfft_plan_s {
     // tensor-core split precision (all-radix-16 schedule)
     const TcVariant* tcv = nullptr;
     const UmmaVariant* umv = nullptr;  // tcgen05 engine (variant 1) instead of mma.sync (variant 0)
-    const DirectVariant* dv = nullptr;  // direct DFT on tcgen05 (variant 2)
+    const DirectVariant* dv = nullptr;     // direct DFT on tcgen05, one tile at a time per CTA (variant 3)
+    const DirectWsVariant* dwv = nullptr;  // the same, warp-specialised and pipelined (variant 2)
     uint16_t* direct_b = nullptr;
     int tc_prec = 0;
     uint32_t* tc_frag = nullptr;
@@ -200,11 +201,14 @@ gbfft_status alloc_stage_tables(float2** dst, int64_t n, const int* radix, int n
     return launch_stage_twiddles(*dst, n, radix, nstages, 0) == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA;
 }
 
-// Direct DFT (variant 2 of the tensor-core dtypes): one split-precision matrix
-// product per 128 transforms, N a multiple of 8 up to 64.
-gbfft_status create_direct(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype) {
+// Direct DFT (variants 2 and 3 of the tensor-core dtypes): one split-precision
+// matrix product per 128 transforms, N a multiple of 8 up to 64; `ws` selects
+// the warp-specialised, pipelined kernel (variant 2) over the kernel that runs
+// each tile's phases one after the other (variant 3).
+gbfft_status create_direct(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, bool ws) {
     const DirectVariant* dv = direct_variant_for(n);
-    if (!dv) return GBFFT_ERR_NOT_FOUND;
+    const DirectWsVariant* dwv = ws ? direct_ws_variant_for(n) : nullptr;
+    if (!dv || (ws && !dwv)) return GBFFT_ERR_NOT_FOUND;
     // BF16x2 keeps ~16 significand bits: one dense product errs by 4-6e-6 relative
     // L2 at every N, above the 1e-6*log2(N) contract for N <= 64.
     if (dtype == GBFFT_C2C_F32_TC_BF16X2) return GBFFT_ERR_UNSUPPORTED_SIZE;
@@ -216,7 +220,8 @@ gbfft_status create_direct(gbfft_plan* out, int64_t n, int64_t batch, int direct
     p->direction = direction;
     p->dtype = dtype;
     p->dv = dv;
-    p->variant = 2;
+    p->dwv = dwv;
+    p->variant = ws ? 2 : 3;
     p->tc_prec = dtype == GBFFT_C2C_F32_TC_FP16X2 ? 0 : 1;
     gbfft_status st = GBFFT_OK;
     if (cudaGetDevice(&p->device) != cudaSuccess || cudaMalloc(&p->status, sizeof(int)) != cudaSuccess ||
@@ -225,8 +230,8 @@ gbfft_status create_direct(gbfft_plan* out, int64_t n, int64_t batch, int direct
         cudaGetLastError();
         st = GBFFT_ERR_OOM;
     }
-    if (st == GBFFT_OK && prepare_direct(*dv) != cudaSuccess) st = GBFFT_ERR_CUDA;
-    if (st == GBFFT_OK && (p->grid_cap = direct_grid(*dv)) <= 0) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && (ws ? prepare_direct_ws(*dwv) : prepare_direct(*dv)) != cudaSuccess) st = GBFFT_ERR_CUDA;
+    if (st == GBFFT_OK && (p->grid_cap = ws ? direct_ws_grid(*dwv) : direct_grid(*dv)) <= 0) st = GBFFT_ERR_CUDA;
     if (st == GBFFT_OK && launch_direct_bmat(p->direct_b, (int)n, p->tc_prec, direction, 0) != cudaSuccess)
         st = GBFFT_ERR_CUDA;
     if (st == GBFFT_OK && cudaDeviceSynchronize() != cudaSuccess) st = GBFFT_ERR_CUDA;
@@ -239,7 +244,7 @@ gbfft_status create_direct(gbfft_plan* out, int64_t n, int64_t batch, int direct
 }
 
 gbfft_status create_tc(gbfft_plan* out, int64_t n, int64_t batch, int direction, int dtype, int engine) {
-    if (engine == 2) return create_direct(out, n, batch, direction, dtype);
+    if (engine == 2 || engine == 3) return create_direct(out, n, batch, direction, dtype, engine == 2);
     const TcVariant* tv = tc_variant_for(n);
     if (!tv) return GBFFT_ERR_UNSUPPORTED_SIZE;
     const UmmaVariant* uv = engine == 1 ? umma_variant_for(n) : nullptr;
@@ -346,7 +351,7 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
             } else if (wv >= 0) {
                 const int limit = dtype == GBFFT_C2C_F32   ? onepass_variants_for(n, nullptr, 0)
                                   : dtype == GBFFT_C2C_F64 ? rows_variants_f64_for(n, nullptr, 0)
-                                                           : 3;
+                                                           : 4;
                 if (wv < limit) variant = wv;
             }
         }
@@ -354,11 +359,13 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     if (dtype == GBFFT_C2C_F64) return create_f64(out, n, batch, direction, variant, k_outer);
     if (dtype != GBFFT_C2C_F32) {
         if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
-        if (variant > 2) return GBFFT_ERR_NOT_FOUND;
+        if (variant > 3) return GBFFT_ERR_NOT_FOUND;
         // default engine: tcgen05 Stockham where it exists (N = 256, 4096), else mma.sync
-        // Stockham (N = 16), else the direct DFT (N = 8, 24, ..., 64)
+        // Stockham (N = 16), else the direct DFT (N = 8, 24, ..., 64): pipelined (variant 2),
+        // except at N = 8, where the one-tile-at-a-time kernel (variant 3) measured 3 % faster
+        const int direct = n == 8 ? 3 : 2;
         const int engine = variant >= 0 ? variant
-                                        : (umma_variant_for(n) ? 1 : (tc_variant_for(n) ? 0 : (direct_variant_for(n) ? 2 : 0)));
+                                        : (umma_variant_for(n) ? 1 : (tc_variant_for(n) ? 0 : (direct_variant_for(n) ? direct : 0)));
         return create_tc(out, n, batch, direction, dtype, engine);
     }
 
@@ -441,6 +448,9 @@ cudaError_t run_device(gbfft_plan p, const void* vin, void* vout, int64_t rows, 
         return launch_rows(*p->rv, p->direction, vin, vout, p->tw64, (long long)rows, 0, s, p->status);
     const float2* in = (const float2*)vin;
     float2* out = (float2*)vout;
+    if (p->kind == kPlanTensorCore && p->dwv)
+        return launch_direct_ws(*p->dwv, p->tc_prec, p->direction, in, out, p->direct_b, (long long)rows, p->grid_cap,
+                                p->status, s);
     if (p->kind == kPlanTensorCore && p->dv)
         return launch_direct(*p->dv, p->tc_prec, p->direction, in, out, p->direct_b, (long long)rows, p->grid_cap,
                              p->status, s);
@@ -774,7 +784,7 @@ gbfft_status gbfft_plan_info(gbfft_plan p, int64_t* n, int64_t* batch, int* dire
     if (nstages) *nstages = ns < kMaxStages ? ns : kMaxStages;
     if (radices)
         for (int i = 0; i < ns && i < kMaxStages; ++i) radices[i] = rad[i];
-    if (variant) *variant = p->kind == kPlanSingle ? p->variant : (p->kind == kPlanTensorCore ? (p->dv ? 2 : (p->umv ? 1 : 0)) : -1);
+    if (variant) *variant = p->kind == kPlanSingle ? p->variant : (p->kind == kPlanTensorCore ? (p->dwv ? 2 : (p->dv ? 3 : (p->umv ? 1 : 0))) : -1);
     if (workspace_bytes) *workspace_bytes = p->ws_bytes;
     return GBFFT_OK;
 }

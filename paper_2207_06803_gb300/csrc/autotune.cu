@@ -150,7 +150,7 @@ gbfft_status gbfft_autotune(int64_t n, int64_t batch, int direction, int dtype, 
         const int nv = rows_variants_f64_for(n, nullptr, 0);
         for (int v = 0; v < nv; ++v) cands.push_back({v, 0});
     } else if (dtype == GBFFT_C2C_F32_TC_FP16X2 || dtype == GBFFT_C2C_F32_TC_BF16X2) {
-        for (int e = 0; e < 3; ++e) cands.push_back({e, 0});  // mma.sync, tcgen05 Stockham, direct DFT
+        for (int e = 0; e < 4; ++e) cands.push_back({e, 0});  // mma.sync, tcgen05 Stockham, direct DFT (2 forms)
     } else {
         return GBFFT_ERR_INVALID_ARG;
     }

@@ -107,6 +107,18 @@ cudaError_t launch_direct_bmat(uint16_t* bm, int n, int prec, int sign, cudaStre
 cudaError_t launch_direct(const DirectVariant& v, int prec, int direction, const float2* in, float2* out,
                           const void* bmat, long long batch, int grid_cap, int* status, cudaStream_t s);
 
+// The direct DFT warp-specialised and pipelined (direct_ws.cu): producers,
+// one MMA thread and an epilogue hand tiles over through two tensor-memory slots.
+struct DirectWsVariant {
+    int n, tpb, smem, tmem_cols;
+    const void* k[2][2];  // [prec][dir]
+};
+const DirectWsVariant* direct_ws_variant_for(int64_t n);
+cudaError_t prepare_direct_ws(const DirectWsVariant& v);
+int direct_ws_grid(const DirectWsVariant& v);
+cudaError_t launch_direct_ws(const DirectWsVariant& v, int prec, int direction, const float2* in, float2* out,
+                             const void* bmat, long long batch, int grid_cap, int* status, cudaStream_t s);
+
 // Ragged-batch plans (ragged.cu).
 struct RaggedState;
 gbfft_status ragged_create(RaggedState** out, const int64_t* n, const int64_t* offsets, int64_t count);

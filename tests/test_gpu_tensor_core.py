@@ -79,7 +79,7 @@ def test_tensor_core_rejects_other_sizes_and_forms():
         gbfft.gbfft_plan_create_variant(256, 4, -1, 1, 2)  # the direct DFT stops at N = 64
     assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
     with pytest.raises(gbfft.GbfftError) as e:
-        gbfft.gbfft_plan_create_variant(64, 4, -1, 1, 3)  # engines are 0, 1 and 2
+        gbfft.gbfft_plan_create_variant(64, 4, -1, 1, 4)  # engines are 0, 1, 2 and 3
     assert e.value.status == gbfft.GBFFT_ERR_NOT_FOUND
     with pytest.raises(gbfft.GbfftError) as e:
         gbfft.gbfft_plan_create_variant(16, 4, -1, 1, 1)  # no tcgen05 engine at N = 16
@@ -142,9 +142,11 @@ def test_tcgen05_engine_matches_gate_and_mma_sync(n, batch, direction, dtype):
 DIRECT_SIZES = (8, 16, 24, 32, 40, 48, 56, 64)
 
 
+@pytest.mark.parametrize("engine", [2, 3])
 @pytest.mark.parametrize("direction", [-1, 1])
-def test_direct_dft_engine_every_size(direction):
-    """Direct DFT on tcgen05 (variant 2, FP16x2): every N, uniform and scaled
+def test_direct_dft_engine_every_size(direction, engine):
+    """Direct DFT on tcgen05 (FP16x2; variant 2 warp-specialised and
+    pipelined, variant 3 one tile at a time per CTA): every N, uniform and scaled
     Gaussian rows (per-row dynamic range 10^+-3), a ragged last tile and
     persistent CTAs walking several tiles, against the oracle."""
     import torch
@@ -156,7 +158,7 @@ def test_direct_dft_engine_every_size(direction):
                  else synth.gaussian_scaled_batch(SEED + n, n, batch))
             d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
             d_out = torch.full_like(d_in, float("nan"))
-            with gbfft.Plan(n, batch, direction, dtype=1, variant=2) as p:
+            with gbfft.Plan(n, batch, direction, dtype=1, variant=engine) as p:
                 p.execute(d_in, d_out)
                 torch.cuda.synchronize()
                 assert gbfft.gbfft_plan_device_status(p.handle) == 0
@@ -168,8 +170,10 @@ def test_direct_dft_engine_every_size(direction):
             assert err.max() <= 1e-6 * math.log2(n), (n, dist, err.max())
 
 
-def test_direct_dft_load_paths_agree():
-    """32-byte-aligned inputs take 32-byte loads, 16-byte-aligned ones 16-byte loads: same bits."""
+@pytest.mark.parametrize("engine", [2, 3])
+def test_direct_dft_load_paths_agree(engine):
+    """Inputs 32-byte or only 16-byte aligned (variant 3 then takes 16-byte
+    loads instead of 32-byte ones): the same bits."""
     import torch
     from paper_2207_06803_gb300 import gbfft
     for n in (8, 24, 64):
@@ -183,7 +187,7 @@ def test_direct_dft_load_paths_agree():
         for buf in (a, b):
             buf.copy_(torch.from_numpy(x.view(np.float32).reshape(-1)).cuda())
             out = torch.empty(2 * n * batch, device="cuda")
-            with gbfft.Plan(n, batch, -1, dtype=1, variant=2) as p:
+            with gbfft.Plan(n, batch, -1, dtype=1, variant=engine) as p:
                 p.execute(buf, out)
             torch.cuda.synchronize()
             outs.append(out)
@@ -197,7 +201,7 @@ def test_direct_dft_in_place_default_engine_and_bf16_rejected():
     x = synth.uniform_batch(SEED, n, batch)
     d = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
     ref = torch.empty_like(d)
-    with gbfft.Plan(n, batch, -1, dtype=1) as p:  # default engine at N = 48: the direct DFT
+    with gbfft.Plan(n, batch, -1, dtype=1) as p:  # default engine at N = 48: the pipelined direct DFT
         assert p.info()["variant"] == 2
         p.execute(d, ref)
         p.execute(d, d)
