@@ -97,12 +97,12 @@ int gbfft_version(void);
  * twiddles stay FP32.  gbfft_plan_create_variant with a tensor-core dtype
  * selects the engine: variant 1 (N = 256, 4096; the default there) issues
  * tcgen05.mma from shared-memory operands into tensor memory and reads results
- * back with tcgen05.ld; variant 0 (the default for N = 16) issues warp-level
+ * back with tcgen05.ld; variant 0 (N = 16, 256, 4096) issues warp-level
  * mma.sync.m16n8k16 on register fragments; variants 2 and 3 (N = 8, 16, 24,
  * ..., 64; FP16x2 only) are the direct DFT: y = F_N x as ONE split-precision
  * real product [yr yi] = [xr xi] [[Fr, Fi], [-Fi, Fr]] per 128 transforms on
  * tcgen05 (M = 128, K = N_out = 2N), no factorisation (the paper's direct-DFT
- * variant, Sec. VI).  Variant 2 (the default at N = 24 ... 64) is warp-
+ * variant, Sec. VI).  Variant 2 (the default at N = 16 ... 64) is warp-
  * specialised: producer warps split rows into tensor memory, one thread issues
  * the MMAs and epilogue warps read the results back, on consecutive tiles at
  * once; variant 3 (the default at N = 8) runs each tile's phases one after the

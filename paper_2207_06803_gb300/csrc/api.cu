@@ -360,12 +360,17 @@ gbfft_status create(gbfft_plan* out, int64_t n, int64_t batch, int direction, in
     if (dtype != GBFFT_C2C_F32) {
         if (k_outer > 0) return GBFFT_ERR_INVALID_ARG;
         if (variant > 3) return GBFFT_ERR_NOT_FOUND;
-        // default engine: tcgen05 Stockham where it exists (N = 256, 4096), else mma.sync
-        // Stockham (N = 16), else the direct DFT (N = 8, 24, ..., 64): pipelined (variant 2),
-        // except at N = 8, where the one-tile-at-a-time kernel (variant 3) measured 3 % faster
-        const int direct = n == 8 ? 3 : 2;
-        const int engine = variant >= 0 ? variant
-                                        : (umma_variant_for(n) ? 1 : (tc_variant_for(n) ? 0 : (direct_variant_for(n) ? direct : 0)));
+        // default engine: tcgen05 Stockham where it exists (N = 256, 4096); for FP16x2 the direct
+        // DFT where it exists (N = 8 ... 64): pipelined (variant 2; at N = 16 6.28 TB/s against 5.43
+        // for the mma.sync Stockham), except at N = 8, where the one-tile-at-a-time kernel
+        // (variant 3) measured 3 % faster; else mma.sync Stockham (variant 0)
+        const bool fp16_direct = dtype == GBFFT_C2C_F32_TC_FP16X2 && direct_variant_for(n);
+        const int engine = variant >= 0         ? variant
+                           : umma_variant_for(n) ? 1
+                           : fp16_direct         ? (n == 8 ? 3 : 2)
+                           : tc_variant_for(n)   ? 0
+                           : direct_variant_for(n) ? 2
+                                                   : 0;
         return create_tc(out, n, batch, direction, dtype, engine);
     }
 

@@ -28,7 +28,8 @@ def run_tc(x, direction, dtype):
     batch, n = x.shape
     d_in = torch.from_numpy(np.ascontiguousarray(x).view(np.float32).reshape(-1)).cuda()
     d_out = torch.empty_like(d_in)
-    with gbfft.Plan(n, batch, direction, dtype) as p:
+    # the DFT_16 Stockham engines (at N = 16 the FP16x2 default is the direct DFT: force mma.sync)
+    with gbfft.Plan(n, batch, direction, dtype, variant=0 if n == 16 else None) as p:
         assert p.info()["radices"] == [16] * int(round(math.log(n, 16)))
         p.execute(d_in, d_out)
         torch.cuda.synchronize()
