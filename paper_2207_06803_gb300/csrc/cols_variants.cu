@@ -36,7 +36,10 @@ static const ColsVariant kCols[] = {
     GBFFT_COLS(112, 28, 16, 7, 4, 4),
     GBFFT_COLS(128, 16, 16, 8, 16),
     GBFFT_COLS(256, 16, 16, 16, 16),
-    GBFFT_COLS(512, 8, 16, 8, 8, 8),
+    // 512: two radix-16 butterflies per thread (512 threads, 62-64 registers: two CTAs per SM); the form with
+    // one radix-8 butterfly per thread (1024 threads, one CTA per SM) ran 16-29 % slower (N = 131072: 2.58 against
+    // 3.12 TB/s; 512 x 1024: 2.44 against 3.15)
+    GBFFT_COLS(512, 16, 16, 16, 16, 2),
 };
 
 const ColsVariant* cols_variant_for(int64_t len) {
