@@ -554,9 +554,11 @@ gbfft_status gbfft_plan_create_nd(gbfft_plan* out, int rank, const int64_t* dims
     if (rows_variants_for(last, cands, kMaxVariantsPerSize) == 0) return GBFFT_ERR_UNSUPPORTED_SIZE;
     if (last % 16 != 0) return GBFFT_ERR_UNSUPPORTED_SIZE;  // column kernels take 16 columns per CTA
     const ColsVariant* cv[2] = {nullptr, nullptr};
+    int64_t stride = last;  // columns of the axis pass = product of the later dimensions
     for (int ax = rank - 2, c = 0; ax >= 0; --ax, ++c) {
-        cv[c] = cols_variant_for(dims[ax]);
+        cv[c] = cols_variant_for_nd(dims[ax], stride);
         if (!cv[c]) return GBFFT_ERR_UNSUPPORTED_SIZE;
+        stride *= dims[ax];
     }
     int64_t total = 1;
     for (int i = 0; i < rank; ++i) total *= dims[i];

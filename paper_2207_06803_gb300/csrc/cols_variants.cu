@@ -48,6 +48,20 @@ const ColsVariant* cols_variant_for(int64_t len) {
     return nullptr;
 }
 
+// Short column lengths for the multi-dimensional plans' axis passes: 64 columns per
+// CTA (128 or 256 threads instead of 32 or 64, so that an SM holds enough loads in
+// flight), used where the axis's row stride is a multiple of 64.
+static const ColsVariant kColsWide[] = {
+    GBFFT_COLS(8, 4, 64, 2, 4),
+    GBFFT_COLS(16, 4, 64, 4, 4),
+};
+
+const ColsVariant* cols_variant_for_nd(int64_t len, int64_t ncols) {
+    for (const ColsVariant& v : kColsWide)
+        if (v.len == len && ncols % v.c == 0) return &v;
+    return cols_variant_for(len);
+}
+
 const ColsVariant* cols_variants(int* count) {
     *count = (int)(sizeof(kCols) / sizeof(kCols[0]));
     return kCols;

@@ -52,6 +52,7 @@ struct ColsVariant {
     const void* k2i;
 };
 
+const ColsVariant* cols_variant_for_nd(int64_t len, int64_t ncols);  // ND axis passes: wider CTAs where the stride allows
 const ColsVariant* cols_variant_for(int64_t len);
 const ColsVariant* cols_variants(int* count);
 cudaError_t prepare_cols(const ColsVariant& v);
