@@ -59,8 +59,8 @@ struct ColumnIO {
 
 // VA: phase A by groups of K consecutive elements (16-byte loads; each destination column receives
 // consecutive slots from consecutive threads), else element by element (8-byte loads at stride TPB).
-template <int N, int K, int S, int TPB, int PS, bool VA, int... Rs>
-__global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, 1024 / TPB)
+template <int N, int K, int S, int TPB, int PS, bool VA, int MINB, int... Rs>
+__global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, MINB)
     k_stockham_cluster(const float2* in, float2* out, const float2* __restrict__ tw, long long batch) {
     constexpr int M = N / K;
     constexpr int E = capacity_of_r<M, 1, TPB, Rs...>();
@@ -157,7 +157,7 @@ __global__ void __cluster_dims__(K, 1, 1) __launch_bounds__(TPB, 1024 / TPB)
     cluster_sync_relaxed();  // no CTA leaves while the others still read its column
 }
 
-template <int N, int K, int TPB, int PS, bool VA, int... Rs>
+template <int N, int K, int TPB, int PS, bool VA, int MINB, int... Rs>
 RowsVariant make_cluster_variant() {
     constexpr int M = N / K;
     return RowsVariant{kRowsCluster,
@@ -169,11 +169,14 @@ RowsVariant make_cluster_variant() {
                        (int)sizeof...(Rs) + 1,
                        {Rs..., K},
                        (int)(smem_elems<1, M, PS>() * sizeof(float2)),
-                       (const void*)&k_stockham_cluster<N, K, -1, TPB, PS, VA, Rs...>,
-                       (const void*)&k_stockham_cluster<N, K, +1, TPB, PS, VA, Rs...>};
+                       (const void*)&k_stockham_cluster<N, K, -1, TPB, PS, VA, MINB, Rs...>,
+                       (const void*)&k_stockham_cluster<N, K, +1, TPB, PS, VA, MINB, Rs...>};
 }
 
-#define GBFFT_CLUSTER(N, K, TPB, PS, VA, ...) make_cluster_variant<N, K, TPB, PS, VA, __VA_ARGS__>()
+// Register caps from __launch_bounds__(TPB, 1024 / TPB): up to 16 complex per thread.
+#define GBFFT_CLUSTER(N, K, TPB, PS, VA, ...) make_cluster_variant<N, K, TPB, PS, VA, 1024 / TPB, __VA_ARGS__>()
+// Two CTAs per SM whatever TPB (up to 128 registers): schedules with up to 32 complex per thread.
+#define GBFFT_CLUSTER2(N, K, TPB, PS, VA, ...) make_cluster_variant<N, K, TPB, PS, VA, 2, __VA_ARGS__>()
 
 // The radix list of a variant is the column schedule followed by K.  The
 // first entry of each length is its cluster default: a CTA pair whose column
@@ -203,6 +206,7 @@ const RowsVariant kCluster[] = {
     GBFFT_CLUSTER(14336, 2, 448, 4, true, 7, 16, 16, 4),
     GBFFT_CLUSTER(14336, 4, 256, 0, false, 14, 16, 16),
     GBFFT_CLUSTER(14336, 4, 224, 4, true, 7, 16, 16, 2),
+    GBFFT_CLUSTER2(16384, 2, 256, 4, false, 32, 16, 16),  // two butterflies per thread: 0.92x (512 threads: 0.86x)
     GBFFT_CLUSTER(16384, 2, 512, 4, false, 16, 16, 16, 2),
     GBFFT_CLUSTER(16384, 2, 512, 4, false, 32, 16, 16),
     GBFFT_CLUSTER(16384, 4, 256, 4, true, 16, 16, 16),
@@ -222,7 +226,7 @@ const RowsVariant kCluster[] = {
 // Lengths whose default plan is the cluster kernel (variant 0) rather than Eq. 2 as two passes:
 // where it measured faster on GB300 (2^26 points): on a CTA pair, 5120 1.18x the two passes, 6144
 // 1.11x, 7168 1.08x, 8192 1.06x, 10240 1.07x.  At 12288 / 14336 / 16384 the best cluster variants
-// reach 0.95x / 1.01x / 0.86x (384-512-thread CTAs, two per SM), so the two passes stay the default.
+// reach 0.95x / 1.01x / 0.92x, so the two passes stay the default.
 bool cluster_is_default(int64_t n) { return n == 5120 || n == 6144 || n == 7168 || n == 8192 || n == 10240; }
 
 int cluster_variants_for(int64_t n, const RowsVariant** out, int max_out) {
