@@ -385,7 +385,7 @@ def run_gpu(args):
             stream.synchronize()
             rows = synth.sample_rows(seed + n, batch, 256)
             y = sampled_rows(torch, np, d_out, batch, n, rows)
-            x = flat.reshape(batch, n)[rows]
+            x = flat[: batch * n].reshape(batch, n)[rows]  # (--sizes may name lengths that do not divide TOTAL)
             oracle_acc.setdefault(str(n), {})["fwd" if direction < 0 else "inv"] = \
                 accuracy_vs_oracle(y, x, direction, gate(n, FP32_GATE))
 
