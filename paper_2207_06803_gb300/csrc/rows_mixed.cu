@@ -1,6 +1,6 @@
 // Single-pass variants for lengths p * 2^k (p = 3, 5, 7) up to 4096.  The
-// first entry of each length is its default.  From 10 to 56 that is the
-// one-row-per-thread kernel (GBFFT_SMALL2); above, a GBFFT_ROWS_T schedule
+// first entry of each length is its default.  From 10 to 48 that is the
+// one-row-per-thread kernel (GBFFT_SMALL2); from 56 up, a GBFFT_ROWS_T schedule
 // (explicit thread count; a stage whose butterflies do not divide the threads
 // runs ceil(butterflies/threads) per thread, guarded) whose first stage is a
 // composite p * 2^j codelet.  Schedules with a lone radix-p stage first and the
@@ -11,8 +11,8 @@
 namespace gbfft {
 
 static const RowsVariant kMixed[] = {
-    // N = 10 ... 56: one row per thread, both Stockham stages in registers, the tile staged through shared
-    // memory with 16-byte accesses (the defaults: 6.1-6.8 TB/s against 5.1-6.4 for the tile kernels below)
+    // N = 10 ... 48: one row per thread, both Stockham stages in registers, the tile staged through shared
+    // memory with 16-byte accesses (the defaults: 6.5-6.8 TB/s against 5.1-6.4 for the tile kernels below)
     GBFFT_SMALL2(10, 128, 5, 2),
     GBFFT_SMALL2(12, 128, 3, 4),
     GBFFT_SMALL2(14, 128, 7, 2),
@@ -21,6 +21,9 @@ static const RowsVariant kMixed[] = {
     GBFFT_SMALL2(28, 128, 7, 4),
     GBFFT_SMALL2(40, 64, 5, 8),
     GBFFT_SMALL2(48, 64, 3, 16),
+    // N = 56: a tile of 64 rows, DFT_14 (prime-factor) then radix 4 on 256 threads, 6.39 TB/s against 6.10-6.20
+    // for one row per thread (56 complex in registers, 166+ registers per thread)
+    GBFFT_ROWS_T(56, 256, 64, 0, 14, 4),
     GBFFT_SMALL2(56, 64, 7, 8),
     // N = 4 as two radix-2 stages (Eq. 1's factorisation; an alternative to the radix-4 codelet)
     GBFFT_ROWS(4, 4, 128, 0, 2, 2),
