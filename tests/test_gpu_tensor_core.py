@@ -172,6 +172,27 @@ def test_direct_dft_engine_every_size(direction, engine):
 
 
 @pytest.mark.parametrize("engine", [2, 3])
+def test_direct_dft_small_batches(engine):
+    """Fewer tiles than CTAs, a single partial tile and tiles just past a
+    multiple of 128 rows: every row against the oracle, device status clean."""
+    import torch
+    from paper_2207_06803_gb300 import gbfft
+    for n in (16, 24, 64):
+        for batch in (1, 5, 127, 129, 1000):
+            x = synth.uniform_batch(SEED + batch, n, batch)
+            d_in = torch.from_numpy(x.view(np.float32).reshape(-1)).cuda()
+            d_out = torch.full_like(d_in, float("nan"))
+            with gbfft.Plan(n, batch, -1, dtype=1, variant=engine) as p:
+                p.execute(d_in, d_out)
+                torch.cuda.synchronize()
+                assert gbfft.gbfft_plan_device_status(p.handle) == 0
+            y = d_out.cpu().numpy().view(np.complex64).reshape(batch, n)
+            ref = oracle.dft(x.astype(np.complex128), -1, nthreads=ncpu())
+            err = row_rel_l2(y, ref)
+            assert np.all(np.isfinite(err)) and err.max() <= 1e-6 * math.log2(n), (n, batch, err.max())
+
+
+@pytest.mark.parametrize("engine", [2, 3])
 def test_direct_dft_load_paths_agree(engine):
     """Inputs 32-byte or only 16-byte aligned (variant 3 then takes 16-byte
     loads instead of 32-byte ones): the same bits."""
